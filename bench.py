@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused D2Q9/D2Q5 MRT porous-media LB step.
+
+Workload (default): side-heated porous cavity of 4096 x 4096 nodes, Ra = 1e6,
+Da = 1e-4, porosity 0.4, Pr = 1, FP32 deviations (one "step" = one time step
+of the whole lattice).  Prints ONE JSON line (rank 0).
+
+  value     coupled MLUPS (nodes x steps / s / 1e6), device-resident state,
+            CUDA events on the library's stream around exactly --steps steps.
+  roofline  the step kernel (the only kernel in the timed region) against the
+            measured HBM copy bandwidth: algorithmic bytes = every population
+            read once and written once (FP32: 28 x 4 = 112 B per node-step).
+  e2e       same metric through the public API from host memory: the initial
+            state is loaded from a host checkpoint (H2D), every step is
+            followed by a Nusselt read-back (D2H), the final state is saved to
+            host (D2H); host wall clock.
+  cpu_baseline  the FP64 CPU oracle, as it stands, on the host cores, on a
+            bounded number of steps of the same lattice.
+  variants  FP64 and FP16-storage throughput of the same lattice, and the mean
+            Nusselt number of FP32 / FP16 against FP64 at equal step counts.
+
+--impl reference times the oracle instead (the CPU reference of the method).
+Under torchrun (WORLD_SIZE > 1) every rank runs an independent replica of the
+workload on its own GPU (the cavity path has no data-path collective here);
+value = all ranks' node updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS & % HBM roofline, FP32 vs FP64 at stated Nu error; adjoint MLUPS"
+BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4, "f16": 28 * 2}
+DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-arith"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16"])
+    ap.add_argument("--no-extras", action="store_true", help="only the timed device leg")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(n):
+    return dict(workload=f"side-heated porous cavity {n}x{n}", nx=n, ny=n, Ra=1e6, Da=1e-4, phi=0.4,
+                Pr=1.0, Ma=0.1, boundary="NEE walls, hot left / cold right / adiabatic top-bottom",
+                inputs_vs_L2="state larger than L2 (no flush needed)" if n >= 1024 else "L2-resident")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in (getattr(self, "out", "") or "").strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[2]) for r in rows)}
+
+
+# ---- distributed plumbing ---------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- legs ----------------------------------------------------------------------------
+
+def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=True):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    w = workload(n)
+    cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=precision, Pr=w["Pr"], Ma=w["Ma"])
+    cav.step(warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(gpu_index)
+    with clk:
+        e0.record(cav.stream)
+        cav.step(steps)
+        e1.record(cav.stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    obs = cav.observables()
+    cav.close()
+    return ms, obs, clk.summary()
+
+
+def e2e_leg(n, precision, steps):
+    """Public API from host memory: load a host checkpoint, step with a
+    Nusselt read-back after every step, save the final state to host."""
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    w = workload(n)
+    kw = dict(Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=precision, Pr=w["Pr"], Ma=w["Ma"])
+    src = Cavity(n, n, **kw)
+    blob = src.save()  # the job's initial state, in host memory
+    src.close()
+    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = memoryview(blob)
+    del blob
+    import ctypes as C
+
+    from paper_1308_2071_gb300 import _lib
+
+    lib = _lib.load()
+    cav = Cavity(n, n, **kw)
+    out = torch.empty(len(pinned), dtype=torch.uint8, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _lib.check(lib.lbm_load(cav.handle, C.c_void_p(pinned.data_ptr()), len(pinned)), cav.handle)
+    nus = []
+    for _ in range(steps):
+        cav.step(1)
+        nus.append(cav.nusselt())
+    _lib.check(lib.lbm_save(cav.handle, C.c_void_p(out.data_ptr()), len(out)), cav.handle)
+    t1 = time.perf_counter()
+    cav.close()
+    mlups = n * n * steps / (t1 - t0) / 1e6
+    return dict(value=round(mlups, 2), unit="MLUPS", h2d_bytes_per_step=int(len(pinned) / steps),
+                d2h_bytes_per_step=int((len(out) + 16 * steps) / steps), steps=steps,
+                seconds=round(t1 - t0, 3))
+
+
+def cpu_leg(n, seconds, warmup=1, max_steps=None):
+    """The FP64 oracle as it stands, on every host core, on a bounded number of
+    steps of the same lattice; returns (MLUPS, threads, steps, seconds)."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    lat = oracle.derive(n, n, Ra=1e6, Da=1e-4, phi=0.4)
+    o = oracle.Oracle(lat)
+    t = time.perf_counter()
+    o.step(warmup, threads=threads)
+    per = max((time.perf_counter() - t) / max(warmup, 1), 1e-6)
+    k = max(1, int(seconds / per))
+    if max_steps:
+        k = min(k, max_steps)
+    t = time.perf_counter()
+    o.step(k, threads=threads)
+    dt = time.perf_counter() - t
+    return n * n * k / dt / 1e6, threads, k, dt
+
+
+# ---- main -------------------------------------------------------------------------------
+
+def main():
+    a = parse()
+    world, rank, local = dist_init()
+    w = workload(a.size)
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        mlups, threads, k, dt = cpu_leg(a.size, seconds=min(a.cpu_seconds * 4, 120.0),
+                                        warmup=min(a.warmup, 1), max_steps=a.steps)
+        line = dict(metric=METRIC, value=round(mlups, 3), unit="MLUPS", impl="reference", n_gpus=a.gpus,
+                    steps=k, warmup=min(a.warmup, 1), ms_per_step=round(dt / k * 1e3, 3),
+                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    config=dict(w, sample=f"{k} of the requested {a.steps} steps on the full lattice"),
+                    cpu_baseline=dict(value=round(mlups, 3), unit="MLUPS", kind="oracle", cores=threads,
+                                      sample=f"{k} steps of the {a.size}^2 lattice, FP64 oracle"),
+                    e2e=dict(value=round(mlups, 3), unit="MLUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1308_2071_gb300 import _lib
+
+    _lib.load()
+    ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local)
+    ms = max_over_ranks(ms, world)
+    nodes = a.size * a.size
+    mlups = world * nodes * a.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = load_peaks()
+    per_launch_s = ms * 1e-3 / a.steps
+    achieved = nodes * BYTES_PER_NODE[a.precision] / per_launch_s / 1e9
+    roof = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
+                frac=round(achieved / peak, 4), traffic=None, kernel="k_step",
+                algorithmic_bytes_per_launch=nodes * BYTES_PER_NODE[a.precision], peak_source=peak_kind)
+    line = dict(metric=METRIC, value=round(mlups, 2), unit="MLUPS", n_gpus=world, steps=a.steps,
+                warmup=a.warmup, ms_per_step=round(ms / a.steps, 5), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype=DTYPE[a.precision], data="synthetic (seeded, no dataset)",
+                config=dict(w, parallelism="replicas" if world > 1 else "single GPU",
+                            global_batch=world, seq_len=None),
+                roofline=roof, clocks=clocks, gpu_launches=a.steps,
+                nu_hot_at_end=obs["nu_hot"], status=obs["status"])
+    if rank == 0 and not a.no_extras:
+        variants = {}
+        # FP64 and FP16 storage on the same lattice, and Nu against FP64 at equal steps
+        nsteps_cmp = a.warmup + min(a.steps, 1000)
+        for prec in ("f64", "f16"):
+            k = min(a.steps, 1000 if prec == "f64" else a.steps)
+            ms_p, obs_p, _ = device_leg(a.size, prec, k, nsteps_cmp - k, 1, gpu_index=local,
+                                        sample_clocks=False)
+            ach = nodes * BYTES_PER_NODE[prec] / (ms_p * 1e-3 / k) / 1e9
+            variants[prec] = dict(mlups=round(nodes * k / (ms_p * 1e-3) / 1e6, 2),
+                                  hbm_gbs=round(ach, 1), hbm_frac=round(ach / peak, 4), steps=k,
+                                  nu_hot=obs_p["nu_hot"], nu_cold=obs_p["nu_cold"], at_step=nsteps_cmp)
+        _, obs32, _ = device_leg(a.size, "f32", min(a.steps, 1000), nsteps_cmp - min(a.steps, 1000), 1,
+                                 gpu_index=local, sample_clocks=False)
+        nu64 = variants["f64"]["nu_hot"]
+        variants["f32"] = dict(nu_hot=obs32["nu_hot"], at_step=nsteps_cmp)
+        variants["nu_rel_err_f32_vs_f64"] = abs(obs32["nu_hot"] - nu64) / abs(nu64)
+        variants["nu_rel_err_f16_vs_f64"] = abs(variants["f16"]["nu_hot"] - nu64) / abs(nu64)
+        line["variants"] = variants
+        line["e2e"] = e2e_leg(a.size, a.precision, min(a.steps, 1000))
+        mlc, threads, k, dt = cpu_leg(a.size, a.cpu_seconds)
+        line["cpu_baseline"] = dict(value=round(mlc, 3), unit="MLUPS", cores=threads, kind="oracle",
+                                    sample=f"{k} steps of the {a.size}^2 lattice, FP64 oracle, {dt:.1f} s")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

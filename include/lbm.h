@@ -1,0 +1,165 @@
+/*
+ * liblbm: GB300 (sm_103a) implementation of the coupled D2Q9 flow / D2Q5
+ * temperature multiple-relaxation-time lattice Boltzmann step for convection
+ * heat transfer in porous media at the REV scale (Liu, He, Li, Tao,
+ * arXiv:1308.2071, Section 3), with the cavity problem of Section 4.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (LBM_OK = 0 or an LBM_ERR_* code);
+ *    no C++ exception crosses this boundary.  lbm_last_error() describes the
+ *    last failure of a handle.
+ *  - Pointers named *_dev are CUDA device pointers on the device that was
+ *    current when lbm_init() ran; pointers named *_host are host pointers.
+ *  - Fields are dense row-major (ny, nx) arrays with x fastest; node (x, y)
+ *    is element y * nx + x.  Walls lie on the perimeter nodes: x = 0 is the
+ *    hot wall, x = nx - 1 the cold wall, y = 0 and y = ny - 1 the adiabatic
+ *    walls of the side-heated cavity (Section 4.1), so L = nx - 1.
+ *  - Work is enqueued on the stream given to lbm_init(); calls that return
+ *    host values synchronise that stream, the others are stream-ordered.
+ *  - The library owns its state buffers (allocated in lbm_init(), freed in
+ *    lbm_destroy()); caller buffers are never retained past a call.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_ERR_ARG 1      /* invalid argument: tau <= 1/2, phi outside (0, 1], n < 5, ... */
+#define LBM_ERR_CUDA 2     /* a CUDA runtime call failed                                  */
+#define LBM_ERR_DIVERGED 3 /* a non-finite value or |u| >= 1/2 was met on the lattice     */
+#define LBM_ERR_TIMEOUT 4  /* a bounded device-side wait ran out                          */
+#define LBM_ERR_STATE 5    /* call out of order (e.g. adjoint before any forward state)   */
+
+/* storage / arithmetic precision of the populations */
+#define LBM_F64 0            /* FP64 storage, FP64 arithmetic                       */
+#define LBM_F32 1            /* FP32 storage of deviations, FP32 arithmetic         */
+#define LBM_F32_STORE_F16 2  /* FP16 storage of deviations, FP32 arithmetic         */
+
+/* thermal boundary layouts */
+#define LBM_BC_SIDE_HEATED 0 /* Section 4.1: left T_h, right T_c, top/bottom adiabatic */
+#define LBM_BC_COOLED 1      /* Section 4.2: every wall at T_c                         */
+
+/* collision operators */
+#define LBM_MRT 0            /* Eq. 17 and Eq. 34 with the rates of Section 4        */
+#define LBM_LBGK 1           /* every rate 1/tau (the reduction stated after Eq. 24) */
+
+/* Parameters of one cavity.  Physical inputs follow Section 2 (Ra, Da, Pr, J,
+ * porosity), the lattice set-up follows Section 4: rho0 = 1, delta_t = 1,
+ * Eq. 37 (second occurrence) for tau_nu and tau_T, U = sqrt(g beta dT L) =
+ * Ma c_s, K = Da L^2, F_phi from Ergun's relation (Eq. 5). */
+typedef struct {
+    int nx, ny;          /* nodes including the wall nodes, both >= 5                 */
+    double Ra, Da, Pr, J;
+    double phi;          /* porosity (mean porosity when a field is set), in (0, 1]   */
+    double Ma;           /* Mach number (Section 4: 0.1)                               */
+    double sigma, varpi; /* thermal capacity ratio, D2Q5 constant (Section 4: 1, -2) */
+    double Th, Tc;       /* wall temperatures; T0 = (Th + Tc) / 2                      */
+    double Qppp;         /* internal heat source Q''' in lattice units (Eq. 30, 33-36) */
+    int precision;       /* LBM_F64, LBM_F32, LBM_F32_STORE_F16                         */
+    int use_phi_field;   /* 0: uniform phi; 1: per-cell phi from lbm_set_porous_field  */
+    int forchheimer;     /* 1: F_phi of Eq. 5; 0: F_phi = 0 (Brinkman model, Sect. 3.1)*/
+    int thermal_bc;      /* LBM_BC_SIDE_HEATED or LBM_BC_COOLED                          */
+    int adiabatic_order; /* 1: T_b = T_f on adiabatic walls; 2: T_b = (4T_f - T_ff)/3   */
+    int collision;       /* LBM_MRT or LBM_LBGK                                          */
+    int block_x, block_y;/* launch shape of the step kernel; 0 = library default        */
+} lbm_params;
+
+/* Observables of the post-stream state at the current time t (the state the
+ * next collision reads).  Nusselt numbers follow Eq. 38 with a one-sided
+ * fourth-order five-point derivative and the trapezoidal mean over the wall
+ * nodes, accumulated in FP64. */
+typedef struct {
+    long t;              /* time steps taken since lbm_init                            */
+    double nu_hot;       /* mean Nu of the wall x = 0                                  */
+    double nu_cold;      /* mean Nu of the wall x = nx - 1                             */
+    double residual;     /* max|u - u_prev| / max|u| since the previous observables call*/
+    double umax;         /* max |u| over the lattice                                   */
+    double mass;         /* sum over nodes of sum_i f_i (FP64)                         */
+    double heat;         /* sum over nodes of T (FP64)                                 */
+    int status;          /* LBM_OK or LBM_ERR_DIVERGED                                 */
+} lbm_obs;
+
+typedef struct lbm_handle_s* lbm_handle;
+
+/* Fills p with the defaults of Section 4 for an nx-by-ny side-heated cavity:
+ * Pr = 1, J = 1, Ma = 0.1, sigma = 1, varpi = -2, Th = 1, Tc = 0, Q''' = 0,
+ * FP32, uniform porosity, Ergun F_phi, first-order adiabatic walls, MRT. */
+void lbm_params_default(lbm_params* p, int nx, int ny, double Ra, double Da, double phi);
+
+/* Creates a cavity (Section 4.1 set-up) on the current CUDA device.
+ * stream: a cudaStream_t (NULL = legacy default stream) on which all work of
+ * the handle is enqueued.  Initial state (a reading of Section 4, where the
+ * paper says only "uniform"): u = 0, phi p = rho0 c_s^2, T = T0, then the
+ * non-equilibrium extrapolation wall rule once.  Errors: LBM_ERR_ARG for an
+ * invalid p (tau <= 1/2, phi outside (0, 1], nx or ny < 5, lattice too large
+ * for 32-bit offsets), LBM_ERR_CUDA. *out is NULL on failure. */
+int lbm_init(const lbm_params* p, void* stream, lbm_handle* out);
+
+/* Sets a per-cell porosity field (extension of the homogeneous model of
+ * Section 2: K(phi) and F_phi(phi) follow Eq. 5 per cell, with the particle
+ * diameter fixed so that K(p->phi) = Da L^2).  phi_dev: device array of ny*nx
+ * values in (0, 1), dtype LBM_F64 (double) or LBM_F32 (float); the caller
+ * keeps ownership, the library copies it (to float for the FP32 path, to
+ * half for the FP16-storage path, double for FP64).  Requires
+ * use_phi_field = 1.  Resets the state to the initial state (t = 0).
+ * Errors: LBM_ERR_ARG, LBM_ERR_STATE (use_phi_field = 0), LBM_ERR_CUDA. */
+int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype);
+
+/* Advances nsteps time steps of Eq. 17-18 and Eq. 34-35 with the wall rule
+ * (Section 4), asynchronously on the handle's stream.  Long runs replay a
+ * captured CUDA graph.  Errors: LBM_ERR_ARG (nsteps < 0), LBM_ERR_CUDA. */
+int lbm_step(lbm_handle h, long nsteps);
+
+/* Computes the observables of the current state and, for each non-NULL
+ * pointer, the field: ux_dev, uy_dev (Eq. 21), T_dev (Eq. 36), p_dev (Eq. 23),
+ * each ny*nx device values of double (LBM_F64) or float (other precisions);
+ * wall nodes report their imposed values (u = 0, wall T and p).
+ * Synchronises the stream.  Returns LBM_ERR_DIVERGED (with *out filled) if
+ * the divergence flag was raised by any step since lbm_init. */
+int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev,
+                    void* p_dev);
+
+/* Mean Nusselt numbers (Eq. 38) of the walls x = 0 and x = nx - 1 of the
+ * current state, FP64; reads only the five node columns next to each wall.
+ * Synchronises the stream. */
+int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold);
+
+/* Writes the full post-stream populations of the current state as FP64:
+ * f_dev[9][ny][nx] and g_dev[5][ny][nx] (device, caller-owned), velocity
+ * order of Eq. 8 (rest, E, N, W, S, NE, NW, SW, SE) and Eq. 26.  Used to
+ * compare the lattice with a reference implementation.  Stream-ordered. */
+int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev);
+
+/* Checkpoint / resume.  A checkpoint is the handle's two state buffers
+ * (the last two post-collision lattices, enough to rebuild every observable
+ * and to continue bit-exactly) plus a header (magic, version, nx, ny,
+ * precision, t).  lbm_checkpoint_size() gives the byte count; lbm_save()
+ * writes it into a caller-owned host buffer of at least that size
+ * (synchronises the stream); lbm_load() restores it into a handle created
+ * with the same nx, ny and precision.  Errors: LBM_ERR_ARG (buffer too small,
+ * header mismatch), LBM_ERR_CUDA. */
+int lbm_checkpoint_size(lbm_handle h, size_t* bytes);
+int lbm_save(lbm_handle h, void* host, size_t bytes);
+int lbm_load(lbm_handle h, const void* host, size_t bytes);
+
+/* Current time step count and divergence status (synchronises the stream). */
+int lbm_query(lbm_handle h, long* t, int* status);
+
+/* Releases every resource of the handle (synchronises its stream). */
+int lbm_destroy(lbm_handle h);
+
+/* Text of the last error of h (or of the last failed lbm_init when h is
+ * NULL); valid until the next call on h. */
+const char* lbm_last_error(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,535 @@
+// C-ABI runtime of liblbm (declared in include/lbm.h): parameter set-up of
+// Section 4, state buffers, CUDA-graph replay of long step sequences and the
+// observables round trip.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kGraphSteps = 64;      // steps per captured graph (even: keeps buffer parity)
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8; fixed so FP64 sums are reproducible
+
+thread_local std::string g_init_error;
+
+struct Derived {
+    double L, tau_nu, tau_T, nu, gbeta, K, Fphi, T0, dT;
+};
+
+}  // namespace
+
+struct lbm_handle_s {
+    lbm_params p;
+    Derived dv;
+    CoefSet coef;
+    Geom gm;
+    int precision;
+    size_t esize;
+    size_t buf_bytes;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;  // buf[cur] holds B_n, buf[cur ^ 1] holds B_{n-1}
+    long t = 0;
+    void* phi = nullptr;
+    void* snap = nullptr;
+    int snap_valid = 0;
+    double* partials = nullptr;
+    double* obs_dev = nullptr;
+    double* obs_host = nullptr;
+    int* status_dev = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int bx = 128, by = 2;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_handle h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(lbm_handle h, cudaError_t e, const char* where) {
+    return fail(h, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, expr)                                          \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+    } while (0)
+
+// Section 4 set-up: Eq. 37 (second occurrence) for tau_nu and tau_T,
+// Eq. 24 for nu_e, J = nu_e / nu, U = sqrt(g beta dT L) = Ma c_s, Da = K/L^2,
+// Eq. 5 for F_phi.
+int derive(const lbm_params* p, Derived* dv, std::string* why) {
+    if (p->nx < 5 || p->ny < 5) return *why = "nx and ny must be >= 5", LBM_ERR_ARG;
+    if (!(p->phi > 0.0 && p->phi <= 1.0)) return *why = "phi must lie in (0, 1]", LBM_ERR_ARG;
+    if (!(p->Ra > 0.0) || !(p->Da > 0.0) || !(p->Pr > 0.0) || !(p->J > 0.0) || !(p->Ma > 0.0))
+        return *why = "Ra, Da, Pr, J and Ma must be positive", LBM_ERR_ARG;
+    if (!(p->sigma > 0.0) || !(p->varpi < 1.0) || !(p->varpi > -4.0))
+        return *why = "sigma must be positive and varpi in (-4, 1)", LBM_ERR_ARG;
+    if (!(p->Th > p->Tc)) return *why = "Th must exceed Tc", LBM_ERR_ARG;
+    if (p->precision < LBM_F64 || p->precision > LBM_F32_STORE_F16) return *why = "bad precision", LBM_ERR_ARG;
+    if (p->use_phi_field && !(p->phi < 1.0))
+        return *why = "a porosity field needs a mean porosity below 1", LBM_ERR_ARG;
+    if (p->adiabatic_order != 1 && p->adiabatic_order != 2) return *why = "adiabatic_order is 1 or 2", LBM_ERR_ARG;
+    if (p->thermal_bc != LBM_BC_SIDE_HEATED && p->thermal_bc != LBM_BC_COOLED)
+        return *why = "unknown thermal_bc", LBM_ERR_ARG;
+    if (p->collision != LBM_MRT && p->collision != LBM_LBGK) return *why = "unknown collision", LBM_ERR_ARG;
+    const double cs2 = 1.0 / 3.0, cs = sqrt(cs2);
+    const double L = (double)(p->nx - 1);
+    const double cT2 = (4.0 + p->varpi) / 10.0;
+    dv->L = L;
+    dv->tau_nu = 0.5 + p->Ma * p->J * L / cs * sqrt(p->Pr / p->Ra);
+    dv->tau_T = 0.5 + cs2 * (dv->tau_nu - 0.5) / (p->sigma * cT2 * p->Pr);
+    if (!(dv->tau_nu > 0.5) || !(dv->tau_T > 0.5)) return *why = "relaxation time not above 1/2", LBM_ERR_ARG;
+    dv->nu = cs2 * (dv->tau_nu - 0.5) / p->J;
+    dv->dT = p->Th - p->Tc;
+    const double U = p->Ma * cs;
+    dv->gbeta = U * U / (dv->dT * L);
+    dv->K = p->Da * L * L;
+    dv->Fphi = p->forchheimer ? 1.75 / sqrt(150.0 * p->phi * p->phi * p->phi) : 0.0;
+    dv->T0 = 0.5 * (p->Th + p->Tc);
+    return LBM_OK;
+}
+
+template <class R>
+void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
+    double s[9], z[5];
+    if (p->collision == LBM_LBGK) {
+        for (int k = 0; k < 9; ++k) s[k] = 1.0 / dv.tau_nu;
+        for (int k = 0; k < 5; ++k) z[k] = 1.0 / dv.tau_T;
+    } else {  // Section 4 choices
+        const double sm[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, 1.0 / dv.tau_nu, 1.0 / dv.tau_nu};
+        const double zm[5] = {1.0, 1.0 / dv.tau_T, 1.0 / dv.tau_T, 1.5, 1.5};
+        memcpy(s, sm, sizeof s);
+        memcpy(z, zm, sizeof z);
+    }
+    for (int k = 0; k < 9; ++k) {
+        c->s[k] = (R)s[k];
+        c->hs[k] = (R)(1.0 - 0.5 * s[k]);
+    }
+    for (int k = 0; k < 5; ++k) {
+        c->z[k] = (R)z[k];
+        c->hz[k] = (R)(1.0 - 0.5 * z[k]);
+    }
+    c->gbeta = (R)dv.gbeta;
+    c->T0 = (R)dv.T0;
+    c->dTh = (R)(p->Th - dv.T0);
+    c->dTc = (R)(p->Tc - dv.T0);
+    c->inv_sigma = (R)(1.0 / p->sigma);
+    c->varpi = (R)p->varpi;
+    c->inv_csT2 = (R)(10.0 / (4.0 + p->varpi));
+    c->wt0 = (R)((1.0 - p->varpi) / 5.0);
+    c->wt1 = (R)((4.0 + p->varpi) / 20.0);
+    c->psi0 = (R)(p->Qppp / p->sigma);
+    c->psi3 = (R)(p->varpi * p->Qppp / p->sigma);
+    c->qhalf = (R)(0.5 * p->Qppp / p->sigma);
+    c->phi = (R)p->phi;
+    c->c_lin = (R)(p->phi * dv.nu / dv.K);
+    c->c_quad = (R)(p->phi * dv.Fphi / sqrt(dv.K));
+    // per-cell Ergun (Eq. 5) with d_p^2 fixed by K(phi_bar) = K_bar:
+    // phi nu / K(phi) = 150 nu (1-phi)^2 / (phi^2 d_p^2), phi F_phi / sqrt K = 1.75 (1-phi) / (phi^2 d_p)
+    if (p->phi < 1.0) {
+        const double pb = p->phi;
+        const double dp2 = 150.0 * dv.K * (1.0 - pb) * (1.0 - pb) / (pb * pb * pb);
+        c->a_lin = (R)(150.0 * dv.nu / dp2);
+        c->a_quad = (R)(p->forchheimer ? 1.75 / sqrt(dp2) : 0.0);
+    } else {
+        c->a_lin = (R)0;
+        c->a_quad = (R)0;
+    }
+}
+
+void free_handle(lbm_handle h) {
+    if (!h) return;
+    for (int k = 0; k < 2; ++k) {
+        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+        if (h->buf[k]) cudaFree(h->buf[k]);
+    }
+    if (h->phi) cudaFree(h->phi);
+    if (h->snap) cudaFree(h->snap);
+    if (h->partials) cudaFree(h->partials);
+    if (h->obs_dev) cudaFree(h->obs_dev);
+    if (h->status_dev) cudaFree(h->status_dev);
+    if (h->obs_host) cudaFreeHost(h->obs_host);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+StepLaunch step_launch(lbm_handle h, int src, cudaStream_t s) {
+    StepLaunch L;
+    L.precision = h->precision;
+    L.src = h->buf[src];
+    L.dst = h->buf[src ^ 1];
+    L.phi = h->p.use_phi_field ? h->phi : nullptr;
+    L.gm = h->gm;
+    L.bx = h->bx;
+    L.by = h->by;
+    L.status = h->status_dev;
+    L.stream = s;
+    return L;
+}
+
+// State B_{-1} = rest everywhere (zero deviations) in both buffers, then one
+// step: pulling the rest state and applying the wall rule gives the initial
+// post-stream state S_0, whose collision is B_0.
+int reset_state(lbm_handle h) {
+    CK(h, cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->buf[1], 0, h->buf_bytes, h->stream));
+    CK(h, cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->stream));
+    h->cur = 0;
+    CK(h, launch_step(step_launch(h, 0, h->stream), h->coef));
+    h->cur = 1;
+    h->t = 0;
+    h->snap_valid = 0;
+    return LBM_OK;
+}
+
+int capture_graph(lbm_handle h, int parity) {
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int src = parity;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        e = launch_step(step_launch(h, src, h->cap_stream), h->coef);
+        src ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, e, "capture step");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_handle h) {
+    for (int k = 0; k < 2; ++k)
+        if (h->gexec[k]) {
+            cudaGraphExecDestroy(h->gexec[k]);
+            h->gexec[k] = nullptr;
+        }
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_params_default(lbm_params* p, int nx, int ny, double Ra, double Da, double phi) {
+    memset(p, 0, sizeof(*p));
+    p->nx = nx;
+    p->ny = ny;
+    p->Ra = Ra;
+    p->Da = Da;
+    p->phi = phi;
+    p->Pr = 1.0;
+    p->J = 1.0;
+    p->Ma = 0.1;
+    p->sigma = 1.0;
+    p->varpi = -2.0;
+    p->Th = 1.0;
+    p->Tc = 0.0;
+    p->Qppp = 0.0;
+    p->precision = LBM_F32;
+    p->use_phi_field = 0;
+    p->forchheimer = 1;
+    p->thermal_bc = LBM_BC_SIDE_HEATED;
+    p->adiabatic_order = 1;
+    p->collision = LBM_MRT;
+    p->block_x = 0;
+    p->block_y = 0;
+}
+
+int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
+    Derived dv;
+    std::string why;
+    int rc = derive(p, &dv, &why);
+    if (rc != LBM_OK) return fail(nullptr, rc, why);
+
+    lbm_handle h = new lbm_handle_s();
+    h->p = *p;
+    h->dv = dv;
+    h->precision = p->precision;
+    h->esize = p->precision == LBM_F64 ? 8 : (p->precision == LBM_F32 ? 4 : 2);
+    const int align = (int)(128 / h->esize);
+    const long pitch = ((long)p->nx + align - 1) / align * align;
+    const long plane = pitch * (long)p->ny;
+    if (plane * NPOP >= (1L << 31)) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "lattice too large for 32-bit offsets");
+    }
+    h->gm.nx = p->nx;
+    h->gm.ny = p->ny;
+    h->gm.pitch = (int)pitch;
+    h->gm.plane = (int)plane;
+    h->gm.thermal_bc = p->thermal_bc;
+    h->gm.adi_order = p->adiabatic_order;
+    fill_coef<double>(p, dv, &h->coef.d);
+    fill_coef<float>(p, dv, &h->coef.f);
+    h->bx = p->block_x > 0 ? p->block_x : (p->nx <= 64 ? 64 : 128);
+    h->by = p->block_y > 0 ? p->block_y : 256 / h->bx;
+    if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256");
+    }
+    h->stream = (cudaStream_t)stream;
+    h->buf_bytes = (size_t)plane * NPOP * h->esize;
+
+    cudaError_t e;
+#define CKI(expr)                                                   \
+    do {                                                            \
+        e = (expr);                                                 \
+        if (e != cudaSuccess) {                                     \
+            std::string m_ = std::string(#expr) + ": " + cudaGetErrorString(e); \
+            free_handle(h);                                         \
+            return fail(nullptr, LBM_ERR_CUDA, m_);                 \
+        }                                                           \
+    } while (0)
+    CKI(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CKI(cudaMalloc(&h->buf[0], h->buf_bytes));
+    CKI(cudaMalloc(&h->buf[1], h->buf_bytes));
+    CKI(cudaMalloc(&h->partials, sizeof(double) * 4 * kReduceBlocks));
+    CKI(cudaMalloc(&h->obs_dev, sizeof(double) * 8));
+    CKI(cudaMalloc(&h->status_dev, sizeof(int)));
+    CKI(cudaMallocHost(&h->obs_host, sizeof(double) * 8));
+    const size_t rsz = p->precision == LBM_F64 ? 8 : 4;
+    CKI(cudaMalloc(&h->snap, rsz * 2 * (size_t)p->nx * p->ny));
+    if (p->use_phi_field) {
+        CKI(cudaMalloc(&h->phi, (size_t)plane * h->esize));
+        CKI(cudaMemsetAsync(h->phi, 0, (size_t)plane * h->esize, h->stream));
+    }
+#undef CKI
+    if (p->use_phi_field) {
+        // until a field is set, every cell holds the mean porosity
+        std::string m;
+        const size_t n = (size_t)p->nx * p->ny;
+        double* tmp = nullptr;
+        e = cudaMalloc(&tmp, n * sizeof(double));
+        if (e == cudaSuccess) {
+            double* host = (double*)malloc(n * sizeof(double));
+            for (size_t k = 0; k < n; ++k) host[k] = p->phi;
+            e = cudaMemcpyAsync(tmp, host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = launch_convert_phi(tmp, 1, h->phi, h->precision, h->gm, kReduceBlocks, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            free(host);
+            cudaFree(tmp);
+        }
+        if (e != cudaSuccess) {
+            m = std::string("porosity fill: ") + cudaGetErrorString(e);
+            free_handle(h);
+            return fail(nullptr, LBM_ERR_CUDA, m);
+        }
+    }
+    rc = reset_state(h);
+    if (rc != LBM_OK) {
+        std::string m = h->err;
+        free_handle(h);
+        return fail(nullptr, rc, m);
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "handle was created with use_phi_field = 0");
+    if (!phi_dev) return fail(h, LBM_ERR_ARG, "phi_dev is NULL");
+    if (dtype != LBM_F64 && dtype != LBM_F32) return fail(h, LBM_ERR_ARG, "dtype must be LBM_F64 or LBM_F32");
+    CK(h, launch_convert_phi(phi_dev, dtype == LBM_F64, h->phi, h->precision, h->gm, kReduceBlocks, h->stream));
+    drop_graphs(h);
+    return reset_state(h);
+}
+
+int lbm_step(lbm_handle h, long nsteps) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    long left = nsteps;
+    while (left >= kGraphSteps) {
+        if (!h->gexec[h->cur]) {
+            int rc = capture_graph(h, h->cur);
+            if (rc != LBM_OK) return rc;
+        }
+        CK(h, cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        left -= kGraphSteps;  // even count: cur unchanged
+    }
+    for (; left > 0; --left) {
+        CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
+        h->cur ^= 1;
+    }
+    h->t += nsteps;
+    return LBM_OK;
+}
+
+int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev, void* p_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    ObserveLaunch L;
+    L.precision = h->precision;
+    L.prev = h->buf[h->cur ^ 1];
+    L.phi = h->p.use_phi_field ? h->phi : nullptr;
+    L.gm = h->gm;
+    L.ux = ux_dev;
+    L.uy = uy_dev;
+    L.T = T_dev;
+    L.p = p_dev;
+    L.snap = h->snap;
+    L.snap_valid = h->snap_valid;
+    L.partials = h->partials;
+    L.nblocks = kReduceBlocks;
+    L.L = h->dv.L;
+    L.dT = h->dv.dT;
+    L.status = h->status_dev;
+    L.out = h->obs_dev;
+    L.stream = h->stream;
+    CK(h, launch_observe(L, h->coef));
+    CK(h, cudaMemcpyAsync(h->obs_host, h->obs_dev, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->snap_valid = 1;
+    const double* o = h->obs_host;
+    const double n = (double)h->p.nx * (double)h->p.ny;
+    const int status = o[6] != 0.0 ? LBM_ERR_DIVERGED : LBM_OK;
+    if (out) {
+        out->t = h->t;
+        out->nu_hot = o[0];
+        out->nu_cold = o[1];
+        out->umax = o[2];
+        out->residual = o[2] > 0.0 ? o[3] / o[2] : 0.0;
+        out->mass = n + o[4];  // sum_i w_i rho0 = 1 per node
+        out->heat = n * h->dv.T0 + o[5];
+        out->status = status;
+    }
+    if (status != LBM_OK) return fail(h, status, "divergence flag raised (non-finite value or |u| >= 1/2)");
+    return LBM_OK;
+}
+
+int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    ObserveLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.precision = h->precision;
+    L.prev = h->buf[h->cur ^ 1];
+    L.gm = h->gm;
+    L.partials = h->partials;
+    L.L = h->dv.L;
+    L.dT = h->dv.dT;
+    L.status = h->status_dev;
+    L.out = h->obs_dev;
+    L.stream = h->stream;
+    CK(h, launch_nusselt(L, h->coef));
+    CK(h, cudaMemcpyAsync(h->obs_host, h->obs_dev, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (nu_hot) *nu_hot = h->obs_host[0];
+    if (nu_cold) *nu_cold = h->obs_host[1];
+    return LBM_OK;
+}
+
+int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!f_dev || !g_dev) return fail(h, LBM_ERR_ARG, "f_dev and g_dev are required");
+    ReadStateLaunch L;
+    L.precision = h->precision;
+    L.prev = h->buf[h->cur ^ 1];
+    L.phi = h->p.use_phi_field ? h->phi : nullptr;
+    L.gm = h->gm;
+    L.f = f_dev;
+    L.g = g_dev;
+    L.nblocks = kReduceBlocks;
+    L.stream = h->stream;
+    CK(h, launch_read_state(L, h->coef));
+    return LBM_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, precision;
+    long t;
+    long payload;  // bytes of buffer data that follow
+};
+}  // namespace
+
+int lbm_checkpoint_size(lbm_handle h, size_t* bytes) {
+    if (!h || !bytes) return fail(h, LBM_ERR_ARG, "handle and bytes are required");
+    *bytes = sizeof(CkptHeader) + 2 * h->buf_bytes;
+    return LBM_OK;
+}
+
+int lbm_save(lbm_handle h, void* host, size_t bytes) {
+    if (!h || !host) return fail(h, LBM_ERR_ARG, "handle and host buffer are required");
+    size_t need = sizeof(CkptHeader) + 2 * h->buf_bytes;
+    if (bytes < need) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
+    CkptHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, "LBMCKPT", 8);
+    hd.version = 1;
+    hd.nx = h->p.nx;
+    hd.ny = h->p.ny;
+    hd.precision = h->precision;
+    hd.t = h->t;
+    hd.payload = (long)(2 * h->buf_bytes);
+    memcpy(host, &hd, sizeof hd);
+    char* dst = (char*)host + sizeof hd;
+    // order: B_{n-1}, then B_n
+    CK(h, cudaMemcpyAsync(dst, h->buf[h->cur ^ 1], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(dst + h->buf_bytes, h->buf[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_load(lbm_handle h, const void* host, size_t bytes) {
+    if (!h || !host) return fail(h, LBM_ERR_ARG, "handle and host buffer are required");
+    CkptHeader hd;
+    if (bytes < sizeof hd) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
+    memcpy(&hd, host, sizeof hd);
+    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || hd.version != 1) return fail(h, LBM_ERR_ARG, "not a checkpoint");
+    if (hd.nx != h->p.nx || hd.ny != h->p.ny || hd.precision != h->precision ||
+        hd.payload != (long)(2 * h->buf_bytes) || bytes < sizeof hd + 2 * h->buf_bytes)
+        return fail(h, LBM_ERR_ARG, "checkpoint does not match this handle");
+    const char* src = (const char*)host + sizeof hd;
+    CK(h, cudaMemcpyAsync(h->buf[0], src, h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->buf[1], src + h->buf_bytes, h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->cur = 1;
+    h->t = hd.t;
+    h->snap_valid = 0;
+    return LBM_OK;
+}
+
+int lbm_query(lbm_handle h, long* t, int* status) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (t) *t = h->t;
+    if (status) *status = st ? LBM_ERR_DIVERGED : LBM_OK;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h) {
+    if (!h) return LBM_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,358 @@
+// Device building blocks of the coupled D2Q9 / D2Q5 MRT lattice Boltzmann step
+// (Liu, He, Li, Tao, arXiv:1308.2071, Section 3) on the side-heated cavity of
+// Section 4.
+//
+// Populations are held as deviations from the rest state of the initial
+// condition: d_i = f_i - w_i rho0 (D2Q9) and h_j = g_j - w~_j T0 (D2Q5).  The
+// model is affine in that shift (sum_i e_i w_i = 0, M w rho0 = rho0 (1, -2, 1,
+// 0, ...), N w~ T0 = T0 (1, 0, 0, varpi, 0)), so every formula below is the
+// paper's formula minus its value at rest, with rho0 = 1 and delta_t = 1
+// (Section 4).  Deviations are O(Ma^2) and O(Delta T), which keeps FP32 and
+// FP16 storage accurate.
+//
+// Storage layout (structure of arrays): plane q of a buffer holds population
+// q for every node, row-major with x fastest and a row pitch that is a
+// multiple of 128 bytes; planes 0..8 are f (Eq. 8 order: rest, E, N, W, S,
+// NE, NW, SW, SE), planes 9..13 are g (Eq. 26 order: rest, E, N, W, S).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---- lattice -----------------------------------------------------------------
+
+// D2Q9 velocity components of Eq. 8 (c = 1).
+__host__ __device__ constexpr int ex9(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey9(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+// D2Q9 weights (stated after Eq. 13).
+__host__ __device__ constexpr double w9(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+// D2Q5 velocities of Eq. 26 are the first five D2Q9 velocities.
+
+constexpr int NPOP = 14;  // 9 flow + 5 thermal planes per buffer
+
+// ---- storage conversions ------------------------------------------------------
+
+template <class S, class R> struct Conv;
+template <> struct Conv<double, double> {
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct Conv<float, float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Conv<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// ---- per-launch coefficients ----------------------------------------------------
+
+// Everything a step needs besides the buffers, in the arithmetic type R.
+template <class R> struct Coef {
+    R s[9];       // flow relaxation rates (Eq. 20)
+    R hs[9];      // 1 - s_k / 2
+    R z[5];       // thermal relaxation rates (Eq. 31)
+    R hz[5];      // 1 - zeta_k / 2
+    R gbeta;      // g beta (buoyancy G = g beta (T - T0) j, Section 2)
+    R dTh, dTc;   // wall temperatures minus T0
+    R T0;
+    R inv_sigma;  // 1 / sigma
+    R varpi;      // D2Q5 constant (Eq. 29)
+    R inv_csT2;   // 1 / c_sT^2 = 10 / (4 + varpi)
+    R wt0, wt1;   // D2Q5 weights w~_0 = (1 - varpi)/5, w~_i = (4 + varpi)/20
+    R psi0, psi3; // Psi_0 = Q/sigma, Psi_3 = varpi Q/sigma (Eq. 30)
+    R qhalf;      // Q / (2 sigma), the source part of Eq. 36
+    R phi;        // uniform porosity
+    R c_lin;      // phi nu / K         (uniform porosity)
+    R c_quad;     // phi F_phi / sqrt K (uniform porosity)
+    R a_lin;      // per-cell: phi nu / K      = a_lin  (1 - phi)^2 / phi^2
+    R a_quad;     // per-cell: phi F_phi / sqrt K = a_quad (1 - phi) / phi^2
+};
+
+// Geometry of one lattice in one pair of buffers.
+struct Geom {
+    int nx, ny;
+    int pitch;        // elements per row
+    int plane;        // elements per population plane (pitch * ny)
+    int thermal_bc;   // 0 side-heated, 1 cooled
+    int adi_order;    // 1 or 2
+};
+
+// Porosity-dependent drag coefficients (Eq. 4 and Eq. 5 per cell).
+template <class R> struct Drag {
+    R phi, iphi, c_lin, c_quad;
+};
+
+template <class R, bool FIELD, class P>
+__device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field, int off) {
+    Drag<R> dr;
+    if constexpr (FIELD) {
+        R phi = Conv<P, R>::ld(phi_field + off);
+        R iphi = R(1) / phi;
+        R om = R(1) - phi;
+        R ip2 = iphi * iphi;
+        dr.phi = phi;
+        dr.iphi = iphi;
+        dr.c_lin = c.a_lin * om * om * ip2;
+        dr.c_quad = c.a_quad * om * ip2;
+    } else {
+        dr.phi = c.phi;
+        dr.iphi = R(1) / c.phi;
+        dr.c_lin = c.c_lin;
+        dr.c_quad = c.c_quad;
+    }
+    return dr;
+}
+
+// ---- pull of one node ------------------------------------------------------------
+
+// f_i(x, t+1) = f_i^+(x - e_i, t) (Eq. 18) and g_j likewise (Eq. 35).
+// off = y * pitch + x of the receiving node.
+template <class S, class R>
+__device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& gm, int off,
+                                     R (&d)[9], R (&h)[5]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        d[i] = Conv<S, R>::ld(src + i * gm.plane + off - ey9(i) * gm.pitch - ex9(i));
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        h[j] = Conv<S, R>::ld(src + (9 + j) * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+}
+
+template <class S, class R>
+__device__ __forceinline__ R pull_heat(const S* __restrict__ src, const Geom& gm, int off) {
+    R t = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        t += Conv<S, R>::ld(src + (9 + j) * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+    return t;
+}
+
+// ---- macroscopic values -------------------------------------------------------------
+
+template <class R> struct Macro {
+    R ux, uy;  // velocity (Eq. 21)
+    R dP;      // phi p - rho0 c_s^2 (Eq. 23)
+    R dT;      // T - T0 (Eq. 36)
+    R Fx, Fy;  // total force (Eq. 4)
+    R umag;    // |u|
+};
+
+// Eq. 36, Section 2 buoyancy, Eq. 22, Eq. 21, Eq. 23, Eq. 4 at a fluid node.
+template <class R>
+__device__ __forceinline__ Macro<R> fluid_macros(const Coef<R>& c, const Drag<R>& dr,
+                                                 const R (&d)[9], const R (&h)[5]) {
+    Macro<R> m;
+    m.dT = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+    const R Gy = c.gbeta * m.dT;
+    const R jx = (d[1] - d[3]) + (d[5] - d[6]) - (d[7] - d[8]);
+    const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R vx = jx;
+    const R vy = jy + R(0.5) * dr.phi * Gy;
+    const R l0 = R(0.5) + R(0.25) * dr.c_lin;
+    const R l1 = R(0.5) * dr.c_quad;
+    const R vm = sqrt(vx * vx + vy * vy);
+    const R den = R(1) / (l0 + sqrt(l0 * l0 + l1 * vm));
+    m.ux = vx * den;
+    m.uy = vy * den;
+    m.umag = vm * den;
+    const R uu = m.ux * m.ux + m.uy * m.uy;
+    const R s18 = (d[1] + d[2] + d[3] + d[4]) + (d[5] + d[6] + d[7] + d[8]);
+    // c_s^2 / (1 - w_0) = 3/5 and rho0 s_0(u) = -(2/3) |u|^2 / phi
+    m.dP = R(0.6) * s18 - R(0.4) * uu * dr.iphi;
+    const R drag = dr.c_lin + dr.c_quad * m.umag;
+    m.Fx = -drag * m.ux;
+    m.Fy = -drag * m.uy + dr.phi * Gy;
+    return m;
+}
+
+// ---- collision ------------------------------------------------------------------------
+
+// Eq. 17 with m_eq of Eq. 16 and S of Eq. 19, then f+ = M^-1 m+ (Eq. 18,
+// M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4));
+// Eq. 34 with n_eq of Eq. 29 and Psi of Eq. 30, then g+ = N^-1 n+ (Eq. 35,
+// N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h.
+template <class R>
+__device__ __forceinline__ void collide(const Coef<R>& c, R iphi, const Macro<R>& mc, R (&d)[9],
+                                        R (&h)[5]) {
+    // m = M d (Eq. 9-11), as a deviation from the rest moments
+    const R a = (d[1] + d[2]) + (d[3] + d[4]);
+    const R b = (d[5] + d[6]) + (d[7] + d[8]);
+    const R ex13 = d[1] - d[3], ey24 = d[2] - d[4];
+    const R dx = (d[5] - d[6]) - (d[7] - d[8]);  // diagonal x-momentum
+    const R dy = (d[5] + d[6]) - (d[7] + d[8]);  // diagonal y-momentum
+    const R m0 = d[0] + a + b;
+    const R m1 = R(-4) * d[0] - a + R(2) * b;
+    const R m2 = R(4) * d[0] - R(2) * a + b;
+    const R m3 = ex13 + dx;
+    const R m4 = R(-2) * ex13 + dx;
+    const R m5 = ey24 + dy;
+    const R m6 = R(-2) * ey24 + dy;
+    const R m7 = (d[1] - d[2]) + (d[3] - d[4]);
+    const R m8 = (d[5] - d[6]) + (d[7] - d[8]);
+
+    // m_eq (Eq. 16) minus rest moments
+    const R ux = mc.ux, uy = mc.uy;
+    const R uu = ux * ux + uy * uy;
+    const R q = R(3) * uu * iphi;
+    const R eq1 = R(6) * mc.dP + q;
+    const R eq2 = R(-9) * mc.dP - q;
+    const R eq7 = (ux * ux - uy * uy) * iphi;
+    const R eq8 = ux * uy * iphi;
+    // S (Eq. 19)
+    const R uF = ux * mc.Fx + uy * mc.Fy;
+    const R S1 = R(6) * uF * iphi;
+    const R S7 = R(2) * (ux * mc.Fx - uy * mc.Fy) * iphi;
+    const R S8 = (ux * mc.Fy + uy * mc.Fx) * iphi;
+
+    // Eq. 17: m+ = m - s (m - m_eq) + (1 - s/2) S, scaled by the diagonal of M^-1
+    const R p0 = (m0 - c.s[0] * m0) * R(1.0 / 9.0);
+    const R p1 = (m1 - c.s[1] * (m1 - eq1) + c.hs[1] * S1) * R(1.0 / 36.0);
+    const R p2 = (m2 - c.s[2] * (m2 - eq2) - c.hs[2] * S1) * R(1.0 / 36.0);
+    const R p3 = (m3 - c.s[3] * (m3 - ux) + c.hs[3] * mc.Fx) * R(1.0 / 6.0);
+    const R p4 = (m4 - c.s[4] * (m4 + ux) - c.hs[4] * mc.Fx) * R(1.0 / 12.0);
+    const R p5 = (m5 - c.s[5] * (m5 - uy) + c.hs[5] * mc.Fy) * R(1.0 / 6.0);
+    const R p6 = (m6 - c.s[6] * (m6 + uy) - c.hs[6] * mc.Fy) * R(1.0 / 12.0);
+    const R p7 = (m7 - c.s[7] * (m7 - eq7) + c.hs[7] * S7) * R(0.25);
+    const R p8 = (m8 - c.s[8] * (m8 - eq8) + c.hs[8] * S8) * R(0.25);
+
+    // f+ = M^T p (columns of Eq. 11)
+    const R r1 = p0 - p1 - R(2) * p2;  // common part of the axis directions
+    const R r5 = p0 + R(2) * p1 + p2;  // common part of the diagonals
+    const R x34 = p3 - R(2) * p4, y56 = p5 - R(2) * p6;
+    const R x34d = p3 + p4, y56d = p5 + p6;
+    d[0] = p0 - R(4) * p1 + R(4) * p2;
+    d[1] = r1 + x34 + p7;
+    d[2] = r1 + y56 - p7;
+    d[3] = r1 - x34 + p7;
+    d[4] = r1 - y56 - p7;
+    d[5] = r5 + x34d + y56d + p8;
+    d[6] = r5 - x34d + y56d - p8;
+    d[7] = r5 - x34d - y56d + p8;
+    d[8] = r5 + x34d - y56d - p8;
+
+    // thermal: n = N h (Eq. 27-28), deviation from T0 (1, 0, 0, varpi, 0)
+    const R n0 = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
+    const R n1 = h[1] - h[3];
+    const R n2 = h[2] - h[4];
+    const R n3 = R(-4) * h[0] + (h[1] + h[2]) + (h[3] + h[4]);
+    const R n4 = (h[1] - h[2]) + (h[3] - h[4]);
+    const R T = c.T0 + mc.dT;
+    const R ne1 = ux * T * c.inv_sigma;
+    const R ne2 = uy * T * c.inv_sigma;
+    const R ne3 = c.varpi * mc.dT;
+    const R q0 = (n0 - c.z[0] * (n0 - mc.dT) + c.hz[0] * c.psi0) * R(0.2);
+    const R q1 = (n1 - c.z[1] * (n1 - ne1)) * R(0.5);
+    const R q2 = (n2 - c.z[2] * (n2 - ne2)) * R(0.5);
+    const R q3 = (n3 - c.z[3] * (n3 - ne3) + c.hz[3] * c.psi3) * R(0.05);
+    const R q4 = (n4 - c.z[4] * n4) * R(0.25);
+    h[0] = q0 - R(4) * q3;
+    h[1] = q0 + q1 + q3 + q4;
+    h[2] = q0 + q2 + q3 - q4;
+    h[3] = q0 - q1 + q3 + q4;
+    h[4] = q0 - q2 + q3 - q4;
+}
+
+// ---- wall rule ----------------------------------------------------------------------------
+
+// Inward normal of a node: (0, 0) for fluid nodes, the diagonal at corners.
+struct Normal {
+    int dx, dy;
+};
+__device__ __forceinline__ Normal normal_of(const Geom& gm, int x, int y) {
+    Normal n;
+    n.dx = (x == 0) ? 1 : (x == gm.nx - 1 ? -1 : 0);
+    n.dy = (y == 0) ? 1 : (y == gm.ny - 1 ? -1 : 0);
+    return n;
+}
+
+// Non-equilibrium extrapolation (Section 4, ref. [43]) at wall node (x, y)
+// with inward normal nr: reads the pulled populations of the inner neighbour
+// x_f = x + nr (and of x + 2 nr for the second-order adiabatic variant),
+// writes the wall node's populations into d, h and returns the imposed
+// macroscopic values (u = 0, p_b = p_f, T_b; force phi_b G(T_b) j).
+template <class S, class R, bool FIELD, class P>
+__device__ __forceinline__ Macro<R> wall_node(const Coef<R>& c, const Geom& gm,
+                                              const S* __restrict__ src, const P* phi_field,
+                                              int x, int y, Normal nr, const Drag<R>& drb,
+                                              R (&d)[9], R (&h)[5]) {
+    const int offf = (y + nr.dy) * gm.pitch + (x + nr.dx);
+    R df[9], hf[5];
+    pull<S, R>(src, gm, offf, df, hf);
+    const Drag<R> drf = drag_at<R, FIELD, P>(c, phi_field, offf);
+    const Macro<R> mf = fluid_macros<R>(c, drf, df, hf);
+
+    Macro<R> mb;
+    mb.ux = R(0);
+    mb.uy = R(0);
+    mb.umag = R(0);
+    // p_b = p_f:  P_b = phi_b p_f, P = rho0 c_s^2 + dP
+    if constexpr (FIELD) {
+        mb.dP = (drb.phi * drf.iphi) * (R(1.0 / 3.0) + mf.dP) - R(1.0 / 3.0);
+    } else {
+        mb.dP = mf.dP;
+    }
+    const bool dirichlet = (gm.thermal_bc == 1) || (nr.dx != 0);
+    if (dirichlet) {
+        mb.dT = (gm.thermal_bc == 1) ? c.dTc : (x == 0 ? c.dTh : c.dTc);
+    } else if (gm.adi_order == 2) {
+        const int offff = (y + 2 * nr.dy) * gm.pitch + (x + 2 * nr.dx);
+        const R dTff = pull_heat<S, R>(src, gm, offff) + c.qhalf;
+        mb.dT = (R(4) * mf.dT - dTff) * R(1.0 / 3.0);
+    } else {
+        mb.dT = mf.dT;
+    }
+    mb.Fx = R(0);
+    mb.Fy = drb.phi * c.gbeta * mb.dT;
+
+    // f_b = f_eq(P_b, 0) + f_f - f_eq(P_f, u_f) (Eq. 13-14 as deviations):
+    // f_eq,i - w_i rho0 = 3 w_i dP + s_i(u) (i >= 1), -(5/3) dP + s_0(u) (i = 0)
+    const R ddP = mb.dP - mf.dP;
+    const R ux = mf.ux, uy = mf.uy;
+    const R uu = ux * ux + uy * uy;
+    const R ip = drf.iphi;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R eu = R(ex9(i)) * ux + R(ey9(i)) * uy;
+        const R si = R(w9(i)) * (R(3) * eu + R(4.5) * eu * eu * ip - R(1.5) * uu * ip);
+        const R cP = (i == 0) ? R(-5.0 / 3.0) : R(3.0 * w9(i));
+        d[i] = df[i] - si + cP * ddP;
+    }
+    // g_b = g_eq(T_b, 0) + g_f - g_eq(T_f, u_f) (Eq. 37, first occurrence)
+    const R Tf = c.T0 + mf.dT;
+    const R ddT = mb.dT - mf.dT;
+    const R adv = Tf * c.inv_sigma * c.inv_csT2 * c.wt1;
+    h[0] = hf[0] + c.wt0 * ddT;
+    h[1] = hf[1] + c.wt1 * ddT - adv * ux;
+    h[2] = hf[2] + c.wt1 * ddT - adv * uy;
+    h[3] = hf[3] + c.wt1 * ddT + adv * ux;
+    h[4] = hf[4] + c.wt1 * ddT + adv * uy;
+    return mb;
+}
+
+// Post-stream state of node (x, y) (pull + wall rule) and its macroscopic values.
+template <class S, class R, bool FIELD, class P>
+__device__ __forceinline__ Macro<R> node_state(const Coef<R>& c, const Geom& gm,
+                                               const S* __restrict__ src, const P* phi_field,
+                                               int x, int y, Drag<R>& dr, R (&d)[9], R (&h)[5]) {
+    const int off = y * gm.pitch + x;
+    dr = drag_at<R, FIELD, P>(c, phi_field, off);
+    const Normal nr = normal_of(gm, x, y);
+    if (nr.dx == 0 && nr.dy == 0) {
+        pull<S, R>(src, gm, off, d, h);
+        return fluid_macros<R>(c, dr, d, h);
+    }
+    return wall_node<S, R, FIELD, P>(c, gm, src, phi_field, x, y, nr, dr, d, h);
+}
+
+}  // namespace lbm

@@ -1,0 +1,151 @@
+"""Python face of liblbm: a cavity of the porous-media MRT lattice Boltzmann
+model (arXiv:1308.2071, Section 3 and 4) driven through the C-ABI.
+
+PyTorch supplies device memory (field outputs, porosity input) and the CUDA
+stream; every step of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+PRECISIONS = {"f64": L.LBM_F64, "f32": L.LBM_F32, "f16": L.LBM_F32_STORE_F16}
+
+
+def make_params(nx: int, ny: int, Ra: float, Da: float, phi: float, precision: str = "f32",
+                **kw) -> L.Params:
+    """lbm_params with the Section 4 defaults, overridden by keyword arguments
+    (Pr, J, Ma, sigma, varpi, Th, Tc, Qppp, use_phi_field, forchheimer,
+    thermal_bc, adiabatic_order, collision, block_x, block_y)."""
+    p = L.Params()
+    L.load().lbm_params_default(C.byref(p), nx, ny, Ra, Da, phi)
+    p.precision = PRECISIONS[precision]
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Cavity:
+    """One cavity on the current CUDA device.  Work runs on `stream`
+    (default: the current torch stream)."""
+
+    def __init__(self, nx: int, ny: int, Ra: float, Da: float, phi: float, precision: str = "f32",
+                 stream: torch.cuda.Stream | None = None, phi_field: torch.Tensor | None = None, **kw):
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device")
+        lib = L.load()
+        if phi_field is not None:
+            kw.setdefault("use_phi_field", 1)
+        self.params = make_params(nx, ny, Ra, Da, phi, precision, **kw)
+        self.nx, self.ny = nx, ny
+        self.precision = precision
+        self.stream = stream or torch.cuda.current_stream()
+        self.device = self.stream.device
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lbm_init(C.byref(self.params), C.c_void_p(self.stream.cuda_stream), C.byref(self._h))
+        L.check(rc, None)
+        if phi_field is not None:
+            self.set_porous_field(phi_field)
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            L.load().lbm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    @property
+    def field_dtype(self) -> torch.dtype:
+        return torch.float64 if self.precision == "f64" else torch.float32
+
+    # -- operations --
+    def set_porous_field(self, phi: torch.Tensor):
+        """Per-cell porosity (ny, nx) on this device, float32 or float64; resets to t = 0."""
+        phi = phi.to(self.device).contiguous()
+        if phi.shape != (self.ny, self.nx):
+            raise ValueError(f"porosity field must be ({self.ny}, {self.nx})")
+        dt = {torch.float64: L.LBM_F64, torch.float32: L.LBM_F32}[phi.dtype]
+        self._sync_inputs(phi)
+        L.check(L.load().lbm_set_porous_field(self._h, C.c_void_p(phi.data_ptr()), dt), self._h)
+
+    def step(self, n: int = 1) -> "Cavity":
+        L.check(L.load().lbm_step(self._h, int(n)), self._h)
+        return self
+
+    def observables(self, fields: bool = False, check: bool = True) -> dict:
+        """Nusselt numbers, residual, |u|max, mass and heat sums (FP64); with
+        fields=True also ux, uy, T, p as (ny, nx) tensors."""
+        obs = L.Obs()
+        ptrs = [None] * 4
+        out = {}
+        if fields:
+            ts = [torch.empty((self.ny, self.nx), dtype=self.field_dtype, device=self.device)
+                  for _ in range(4)]
+            out.update(zip(("ux", "uy", "T", "p"), ts))
+            ptrs = [C.c_void_p(t.data_ptr()) for t in ts]
+        rc = L.load().lbm_observables(self._h, C.byref(obs), *ptrs)
+        if rc != L.LBM_ERR_DIVERGED or check:
+            L.check(rc, self._h)
+        out.update(t=obs.t, nu_hot=obs.nu_hot, nu_cold=obs.nu_cold, residual=obs.residual,
+                   umax=obs.umax, mass=obs.mass, heat=obs.heat, status=obs.status)
+        return out
+
+    def nusselt(self):
+        """(Nu of the hot wall, Nu of the cold wall), FP64 (Eq. 38)."""
+        a, b = C.c_double(), C.c_double()
+        L.check(L.load().lbm_nusselt(self._h, C.byref(a), C.byref(b)), self._h)
+        return a.value, b.value
+
+    def read_state(self):
+        """Full FP64 post-stream populations f (9, ny, nx) and g (5, ny, nx)."""
+        f = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)
+        g = torch.empty((5, self.ny, self.nx), dtype=torch.float64, device=self.device)
+        L.check(L.load().lbm_read_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr())),
+                self._h)
+        self.stream.synchronize()
+        return f, g
+
+    def save(self) -> bytearray:
+        """Checkpoint (header + both state buffers) as host bytes."""
+        n = C.c_size_t()
+        L.check(L.load().lbm_checkpoint_size(self._h, C.byref(n)), self._h)
+        buf = bytearray(n.value)
+        ptr = (C.c_char * n.value).from_buffer(buf)
+        L.check(L.load().lbm_save(self._h, C.addressof(ptr), n.value), self._h)
+        return buf
+
+    def load(self, blob: bytearray):
+        ptr = (C.c_char * len(blob)).from_buffer(blob)
+        L.check(L.load().lbm_load(self._h, C.addressof(ptr), len(blob)), self._h)
+
+    def query(self):
+        t, st = C.c_long(), C.c_int()
+        L.check(L.load().lbm_query(self._h, C.byref(t), C.byref(st)), self._h)
+        return t.value, st.value
+
+    def _sync_inputs(self, *tensors):
+        # inputs produced on torch's current stream must be ready on ours
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)

@@ -1,0 +1,110 @@
+"""Host-side checks of the C-ABI that need no GPU: the library loads, exports
+every entry point that include/*.h declares, and rejects invalid parameters
+before touching the device."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1308_2071_gb300.build import build
+    from paper_1308_2071_gb300 import _lib
+
+    return _lib.load(build())
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_init", "lbm_set_porous_field", "lbm_step", "lbm_observables", "lbm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1308_2071_gb300 import _lib
+
+    bound = {name for name, _, _ in _lib.SIGNATURES}
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared but not exported"
+        assert name in bound, f"{name} has no Python binding"
+
+
+def test_params_default_follow_section_4(lib):
+    from paper_1308_2071_gb300 import _lib
+
+    p = _lib.Params()
+    lib.lbm_params_default(C.byref(p), 64, 48, 1e4, 1e-2, 0.6)
+    assert (p.nx, p.ny, p.Ra, p.Da, p.phi) == (64, 48, 1e4, 1e-2, 0.6)
+    assert (p.Pr, p.J, p.Ma, p.sigma, p.varpi, p.Th, p.Tc, p.Qppp) == (1.0, 1.0, 0.1, 1.0, -2.0, 1.0, 0.0, 0.0)
+    assert p.precision == _lib.LBM_F32 and p.forchheimer == 1 and p.collision == _lib.LBM_MRT
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("nx", 4, "nx and ny"),
+    ("phi", 0.0, "phi"),
+    ("phi", 1.5, "phi"),
+    ("Ra", -1.0, "positive"),
+    ("varpi", 1.0, "varpi"),
+    ("Tc", 2.0, "Th"),
+    ("precision", 7, "precision"),
+    ("adiabatic_order", 3, "adiabatic"),
+])
+def test_init_rejects_invalid_parameters_on_the_host(lib, field, value, needle):
+    from paper_1308_2071_gb300 import _lib
+
+    p = _lib.Params()
+    lib.lbm_params_default(C.byref(p), 64, 64, 1e4, 1e-2, 0.6)
+    setattr(p, field, value)
+    h = C.c_void_p()
+    rc = lib.lbm_init(C.byref(p), None, C.byref(h))
+    assert rc == _lib.LBM_ERR_ARG
+    assert not h.value
+    assert needle in lib.lbm_last_error(None).decode()
+
+
+def test_tau_at_or_below_one_half_is_rejected(lib):
+    from paper_1308_2071_gb300 import _lib
+
+    p = _lib.Params()
+    lib.lbm_params_default(C.byref(p), 64, 64, 1e4, 1e-2, 0.6)
+    p.Ra = 1e300  # drives tau_nu to 1/2
+    h = C.c_void_p()
+    assert lib.lbm_init(C.byref(p), None, C.byref(h)) == _lib.LBM_ERR_ARG
+    assert "1/2" in lib.lbm_last_error(None).decode()
+
+
+def test_null_handles_are_errors_not_crashes(lib):
+    from paper_1308_2071_gb300 import _lib
+
+    assert lib.lbm_step(None, 1) == _lib.LBM_ERR_ARG
+    assert lib.lbm_destroy(None) == _lib.LBM_OK
+    assert lib.lbm_init(None, None, None) == _lib.LBM_ERR_ARG
+
+
+def test_package_import_loads_nothing_and_fails_loudly_without_library(tmp_path):
+    import paper_1308_2071_gb300 as pkg
+    from paper_1308_2071_gb300 import _lib
+
+    assert pkg.__name__
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="missing"):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (max over the lattice):
+  FP64 path:   populations 1e-13 absolute after one step; fields 1e-10
+               relative (velocity to max|u|, temperature to dT), Nu 1e-10.
+  FP32 path:   one-step populations 2e-7 absolute (FP32 rounding of O(1e-2)
+               deviations plus FP32 arithmetic); long runs per field below.
+  FP16 store:  one-step populations 3e-5 absolute (half rounding of the
+               deviations); long runs per field below.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, derive
+import oracle.orc as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def cavity(*a, **k):
+    from paper_1308_2071_gb300 import Cavity
+
+    return Cavity(*a, **k)
+
+
+def np_(t):
+    return t.double().cpu().numpy()
+
+
+def field_errors(obs, o):
+    oux, ouy, op, oT = o.macros()
+    umax = max(np.abs(oux).max(), np.abs(ouy).max(), 1e-300)
+    eu = max(np.abs(np_(obs["ux"]) - oux).max(), np.abs(np_(obs["uy"]) - ouy).max()) / umax
+    eT = np.abs(np_(obs["T"]) - oT).max() / (o.lat.Th - o.lat.Tc)
+    ep = np.abs(np_(obs["p"]) - op).max() / np.abs(op).max()
+    onl, onr = o.nusselt()
+    en = max(abs(obs["nu_hot"] - onl) / abs(onl), abs(obs["nu_cold"] - onr) / abs(onr))
+    return eu, eT, ep, en
+
+
+# ---- one-step map, every population, several tiles and ragged tails ----------
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 2e-7), ("f16", 3e-5)])
+@pytest.mark.parametrize("shape", [(17, 13), (64, 64), (131, 70), (300, 257)])
+def test_one_step_populations(precision, tol, shape, nthreads):
+    nx, ny = shape
+    Ra, Da, phi = 1e5, 1e-2, 0.6
+    cav = cavity(nx, ny, Ra=Ra, Da=Da, phi=phi, precision=precision)
+    lat = derive(nx, ny, Ra=Ra, Da=Da, phi=phi)
+    o = Oracle(lat)
+    for n in (0, 37, 400):
+        cav.step(n - cav.query()[0])
+        f, g = cav.read_state()
+        o.set_state(np_(f), np_(g))
+        o.step(1, threads=nthreads)
+        cav.step(1)
+        f1, g1 = cav.read_state()
+        fo, go = o.state()
+        ef = np.abs(np_(f1) - fo).max()
+        eg = np.abs(np_(g1) - go).max()
+        assert ef < tol and eg < tol, (n, ef, eg)
+    cav.close()
+
+
+def test_initial_state_matches_oracle():
+    for prec in ("f64", "f32", "f16"):
+        cav = cavity(20, 16, Ra=1e4, Da=1e-2, phi=0.6, precision=prec)
+        o = Oracle(derive(20, 16, Ra=1e4, Da=1e-2, phi=0.6))
+        f, g = cav.read_state()
+        fo, go = o.state()
+        assert np.abs(np_(f) - fo).max() < 1e-15
+        assert np.abs(np_(g) - go).max() < 1e-15
+        cav.close()
+
+
+# ---- long runs of the cavity of config 1 ---------------------------------------------
+
+@pytest.fixture(scope="module")
+def oracle_c1(nthreads):
+    """64^2, Ra = 1e4, Da = 1e-2, phi = 0.6, Pr = 1: states at 200 and 20000 steps."""
+    o = Oracle(derive(64, 64, Ra=1e4, Da=1e-2, phi=0.6))
+    snaps = {}
+    for n in (200, 20000):
+        o.step(n - o.t, threads=nthreads)
+        snaps[n] = (o.macros(), o.nusselt())
+    return snaps
+
+
+class _Snap:
+    def __init__(self, macros, nus, lat):
+        self._m, self._n, self.lat = macros, nus, lat
+
+    def macros(self):
+        return self._m
+
+    def nusselt(self):
+        return self._n
+
+
+@pytest.mark.parametrize("precision,tol_u,tol_T,tol_nu", [
+    ("f64", 1e-10, 1e-10, 1e-10),
+    ("f32", 2e-4, 2e-5, 2e-4),
+    ("f16", 2e-2, 2e-3, 2e-2),
+])
+def test_config1_fields_and_nusselt(oracle_c1, precision, tol_u, tol_T, tol_nu):
+    lat = derive(64, 64, Ra=1e4, Da=1e-2, phi=0.6)
+    cav = cavity(64, 64, Ra=1e4, Da=1e-2, phi=0.6, precision=precision)
+    for n in (200, 20000):
+        cav.step(n - cav.query()[0])
+        obs = cav.observables(fields=True)
+        eu, eT, ep, en = field_errors(obs, _Snap(*oracle_c1[n], lat))
+        assert eu < tol_u and eT < tol_T and en < tol_nu, (precision, n, eu, eT, ep, en)
+        assert obs["status"] == 0
+    cav.close()
+
+
+# ---- variants of the step --------------------------------------------------------------
+
+def test_lbgk_mode_matches_oracle(nthreads):
+    lat = derive(40, 36, Ra=1e4, Da=1e-2, phi=0.6)
+    tau, tauT = 1 / lat.s[7], 1 / lat.zeta[1]
+    for k in range(9):
+        lat.s[k] = 1 / tau
+    for k in range(5):
+        lat.zeta[k] = 1 / tauT
+    o = Oracle(lat).step(500, threads=nthreads)
+    cav = cavity(40, 36, Ra=1e4, Da=1e-2, phi=0.6, precision="f64", collision=1)
+    cav.step(500)
+    eu, eT, ep, en = field_errors(cav.observables(fields=True), o)
+    assert max(eu, eT, ep, en) < 1e-11, (eu, eT, ep, en)
+
+
+def test_second_order_adiabatic_walls_match_oracle(nthreads):
+    lat = derive(40, 36, Ra=1e5, Da=1e-2, phi=0.6)
+    lat.adiabatic_order = 2
+    o = Oracle(lat).step(700, threads=nthreads)
+    cav = cavity(40, 36, Ra=1e5, Da=1e-2, phi=0.6, precision="f64", adiabatic_order=2)
+    cav.step(700)
+    eu, eT, ep, en = field_errors(cav.observables(fields=True), o)
+    assert max(eu, eT, ep, en) < 1e-11, (eu, eT, ep, en)
+
+
+def test_brinkman_forchheimer_off_matches_oracle(nthreads):
+    lat = derive(40, 40, Ra=1e5, Da=1e-3, phi=0.5)
+    lat.forchheimer = 0
+    o = Oracle(lat).step(600, threads=nthreads)
+    cav = cavity(40, 40, Ra=1e5, Da=1e-3, phi=0.5, precision="f64", forchheimer=0)
+    cav.step(600)
+    eu, eT, ep, en = field_errors(cav.observables(fields=True), o)
+    assert max(eu, eT, ep, en) < 1e-11, (eu, eT, ep, en)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_porosity_field_matches_oracle(precision, tol, nthreads):
+    import torch
+
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    nx, ny = 48, 40
+    phi = perturbed_porosity(ny, nx, phi_bar=0.6, amplitude=0.1, corr_len=6.0, seed=5)
+    lat = derive(nx, ny, Ra=1e5, Da=1e-2, phi=0.6)
+    o = Oracle(lat, phi_field=phi).step(800, threads=nthreads)
+    cav = cavity(nx, ny, Ra=1e5, Da=1e-2, phi=0.6, precision=precision,
+                 phi_field=torch.from_numpy(phi).cuda())
+    cav.step(800)
+    eu, eT, ep, en = field_errors(cav.observables(fields=True), o)
+    assert max(eu, eT, en) < tol, (eu, eT, ep, en)
+
+
+# ---- full size, bench launch configuration ----------------------------------------
+
+def test_full_size_one_step_fp32(nthreads):
+    # 4096^2 cavity of the throughput benchmark (Ra = 1e6, Da = 1e-4, phi = 0.4):
+    # every population after one step, from the GPU's own state, vs the oracle.
+    n = 4096
+    cav = cavity(n, n, Ra=1e6, Da=1e-4, phi=0.4, precision="f32")
+    cav.step(300)
+    f, g = cav.read_state()
+    fh, gh = np_(f), np_(g)
+    del f, g
+    o = Oracle(derive(n, n, Ra=1e6, Da=1e-4, phi=0.4))
+    o.set_state(fh, gh)
+    del fh, gh
+    o.step(1, threads=nthreads)
+    cav.step(1)
+    f1, g1 = cav.read_state()
+    fo, go = o.state()
+    for q in range(9):
+        assert np.abs(np_(f1[q]) - fo[q]).max() < 2e-7, q
+    for q in range(5):
+        assert np.abs(np_(g1[q]) - go[q]).max() < 2e-7, q
+    cav.close()
+
+
+# ---- failure detection, checkpoint ---------------------------------------------------
+
+def test_checkpoint_resume_is_bit_exact():
+    a = cavity(50, 40, Ra=1e5, Da=1e-2, phi=0.6, precision="f32")
+    a.step(123)
+    blob = a.save()
+    a.step(77)
+    ref = a.observables(fields=True)
+    b = cavity(50, 40, Ra=1e5, Da=1e-2, phi=0.6, precision="f32")
+    b.load(blob)
+    assert b.query()[0] == 123
+    b.step(77)
+    got = b.observables(fields=True)
+    for k in ("ux", "uy", "T", "p"):
+        assert np.array_equal(np_(got[k]), np_(ref[k]))
+    assert got["nu_hot"] == ref["nu_hot"]
+
+
+def test_planted_nan_raises_divergence_status():
+    from paper_1308_2071_gb300 import _lib
+
+    cav = cavity(40, 40, Ra=1e5, Da=1e-2, phi=0.6, precision="f32")
+    cav.step(10)
+    blob = cav.save()
+    # the checkpoint payload is two float32 buffers of 14 planes (row pitch 64
+    # floats for nx = 40); plant a NaN in the newer one
+    payload = 14 * 64 * 40 * 4
+    header = len(blob) - 2 * payload
+    arr = np.frombuffer(blob, dtype=np.float32, count=payload // 4, offset=header + payload)
+    k = 20 * 64 + 20  # node (20, 20) of plane 0
+    arr.setflags(write=True)
+    arr[k] = np.nan
+    cav.load(blob)
+    cav.step(3)
+    t, status = cav.query()
+    assert status == _lib.LBM_ERR_DIVERGED
+    with pytest.raises(_lib.LbmError, match="DIVERGED"):
+        cav.observables()
+    assert cav.observables(check=False)["status"] == _lib.LBM_ERR_DIVERGED
