@@ -276,17 +276,16 @@ def main():
     if rank == 0 and not a.no_extras:
         variants = {}
         # FP64 and FP16 storage on the same lattice, and Nu against FP64 at equal steps
-        nsteps_cmp = a.warmup + min(a.steps, 1000)
+        k = min(a.steps, 1000)
+        nsteps_cmp = a.warmup + k
         for prec in ("f64", "f16"):
-            k = min(a.steps, 1000 if prec == "f64" else a.steps)
-            ms_p, obs_p, _ = device_leg(a.size, prec, k, nsteps_cmp - k, 1, gpu_index=local,
+            ms_p, obs_p, _ = device_leg(a.size, prec, k, a.warmup, 1, gpu_index=local,
                                         sample_clocks=False)
             ach = nodes * BYTES_PER_NODE[prec] / (ms_p * 1e-3 / k) / 1e9
             variants[prec] = dict(mlups=round(nodes * k / (ms_p * 1e-3) / 1e6, 2),
                                   hbm_gbs=round(ach, 1), hbm_frac=round(ach / peak, 4), steps=k,
                                   nu_hot=obs_p["nu_hot"], nu_cold=obs_p["nu_cold"], at_step=nsteps_cmp)
-        _, obs32, _ = device_leg(a.size, "f32", min(a.steps, 1000), nsteps_cmp - min(a.steps, 1000), 1,
-                                 gpu_index=local, sample_clocks=False)
+        _, obs32, _ = device_leg(a.size, "f32", k, a.warmup, 1, gpu_index=local, sample_clocks=False)
         nu64 = variants["f64"]["nu_hot"]
         variants["f32"] = dict(nu_hot=obs32["nu_hot"], at_step=nsteps_cmp)
         variants["nu_rel_err_f32_vs_f64"] = abs(obs32["nu_hot"] - nu64) / abs(nu64)

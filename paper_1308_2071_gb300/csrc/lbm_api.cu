@@ -31,7 +31,6 @@ struct lbm_handle_s {
     CoefSet coef;
     Geom gm;
     int precision;
-    size_t esize;
     size_t buf_bytes;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -267,8 +266,9 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     h->p = *p;
     h->dv = dv;
     h->precision = p->precision;
-    h->esize = p->precision == LBM_F64 ? 8 : (p->precision == LBM_F32 ? 4 : 2);
-    const int align = (int)(128 / h->esize);
+    // row pitch in elements: rows of the flow planes and of the thermal planes
+    // both start on 128-byte boundaries (FP64: 16, FP32: 32, FP16 flow: 64)
+    const int align = p->precision == LBM_F64 ? 16 : (p->precision == LBM_F32 ? 32 : 64);
     const long pitch = ((long)p->nx + align - 1) / align * align;
     const long plane = pitch * (long)p->ny;
     if (plane * NPOP >= (1L << 31)) {
@@ -290,7 +290,7 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
         return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256");
     }
     h->stream = (cudaStream_t)stream;
-    h->buf_bytes = (size_t)plane * NPOP * h->esize;
+    h->buf_bytes = state_buffer_bytes(p->precision, (int)plane);
 
     cudaError_t e;
 #define CKI(expr)                                                   \
@@ -312,8 +312,8 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     const size_t rsz = p->precision == LBM_F64 ? 8 : 4;
     CKI(cudaMalloc(&h->snap, rsz * 2 * (size_t)p->nx * p->ny));
     if (p->use_phi_field) {
-        CKI(cudaMalloc(&h->phi, (size_t)plane * h->esize));
-        CKI(cudaMemsetAsync(h->phi, 0, (size_t)plane * h->esize, h->stream));
+        CKI(cudaMalloc(&h->phi, phi_bytes(p->precision, (int)plane)));
+        CKI(cudaMemsetAsync(h->phi, 0, phi_bytes(p->precision, (int)plane), h->stream));
     }
 #undef CKI
     if (p->use_phi_field) {

@@ -11,9 +11,11 @@
 // FP16 storage accurate.
 //
 // Storage layout (structure of arrays): plane q of a buffer holds population
-// q for every node, row-major with x fastest and a row pitch that is a
-// multiple of 128 bytes; planes 0..8 are f (Eq. 8 order: rest, E, N, W, S,
-// NE, NW, SW, SE), planes 9..13 are g (Eq. 26 order: rest, E, N, W, S).
+// q for every node, row-major with x fastest and a row pitch (in elements)
+// that makes every row start on a 128-byte boundary; planes 0..8 are f
+// (Eq. 8 order: rest, E, N, W, S, NE, NW, SW, SE), planes 9..13 are g (Eq. 26
+// order: rest, E, N, W, S).  Flow and thermal planes may use different
+// storage types (see PrecF16); both use the same pitch in elements.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -54,6 +56,56 @@ template <> struct Conv<__half, float> {
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
+
+// ---- precision variants -----------------------------------------------------------
+// SF: storage of the nine flow planes, SG: storage of the five thermal planes,
+// R: arithmetic, P: storage of a per-cell porosity field.
+struct PrecF64 {
+    using SF = double;
+    using SG = double;
+    using R = double;
+    using P = double;
+};
+struct PrecF32 {
+    using SF = float;
+    using SG = float;
+    using R = float;
+    using P = float;
+};
+// FP16 flow deviations (|d| stays near 1e-2, where half rounds to ~4e-6) with
+// FP32 thermal deviations (which reach w~_0 (T_h - T0) = 0.3 at the hot wall,
+// where half would round to ~1.2e-4 and drift the temperature field).
+struct PrecF16 {
+    using SF = __half;
+    using SG = float;
+    using R = float;
+    using P = float;
+};
+
+// Read-only typed view of one state buffer: 9 flow planes then 5 thermal planes.
+template <class T> struct Src {
+    const typename T::SF* __restrict__ f;
+    const typename T::SG* __restrict__ g;
+};
+template <class T> struct Dst {
+    typename T::SF* __restrict__ f;
+    typename T::SG* __restrict__ g;
+};
+template <class T> __host__ __device__ inline Src<T> src_view(const void* base, int plane) {
+    Src<T> s;
+    s.f = (const typename T::SF*)base;
+    s.g = (const typename T::SG*)((const char*)base + (size_t)9 * plane * sizeof(typename T::SF));
+    return s;
+}
+template <class T> __host__ __device__ inline Dst<T> dst_view(void* base, int plane) {
+    Dst<T> d;
+    d.f = (typename T::SF*)base;
+    d.g = (typename T::SG*)((char*)base + (size_t)9 * plane * sizeof(typename T::SF));
+    return d;
+}
+template <class T> __host__ __device__ constexpr size_t buffer_bytes(int plane) {
+    return (size_t)plane * (9 * sizeof(typename T::SF) + 5 * sizeof(typename T::SG));
+}
 
 // ---- per-launch coefficients ----------------------------------------------------
 
@@ -118,23 +170,25 @@ __device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field,
 
 // f_i(x, t+1) = f_i^+(x - e_i, t) (Eq. 18) and g_j likewise (Eq. 35).
 // off = y * pitch + x of the receiving node.
-template <class S, class R>
-__device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& gm, int off,
-                                     R (&d)[9], R (&h)[5]) {
+template <class T>
+__device__ __forceinline__ void pull(const Src<T>& src, const Geom& gm, int off,
+                                     typename T::R (&d)[9], typename T::R (&h)[5]) {
+    using R = typename T::R;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        d[i] = Conv<S, R>::ld(src + i * gm.plane + off - ey9(i) * gm.pitch - ex9(i));
+        d[i] = Conv<typename T::SF, R>::ld(src.f + i * gm.plane + off - ey9(i) * gm.pitch - ex9(i));
 #pragma unroll
     for (int j = 0; j < 5; ++j)
-        h[j] = Conv<S, R>::ld(src + (9 + j) * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+        h[j] = Conv<typename T::SG, R>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
 }
 
-template <class S, class R>
-__device__ __forceinline__ R pull_heat(const S* __restrict__ src, const Geom& gm, int off) {
+template <class T>
+__device__ __forceinline__ typename T::R pull_heat(const Src<T>& src, const Geom& gm, int off) {
+    using R = typename T::R;
     R t = 0;
 #pragma unroll
     for (int j = 0; j < 5; ++j)
-        t += Conv<S, R>::ld(src + (9 + j) * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+        t += Conv<typename T::SG, R>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
     return t;
 }
 
@@ -281,15 +335,17 @@ __device__ __forceinline__ Normal normal_of(const Geom& gm, int x, int y) {
 // x_f = x + nr (and of x + 2 nr for the second-order adiabatic variant),
 // writes the wall node's populations into d, h and returns the imposed
 // macroscopic values (u = 0, p_b = p_f, T_b; force phi_b G(T_b) j).
-template <class S, class R, bool FIELD, class P>
-__device__ __forceinline__ Macro<R> wall_node(const Coef<R>& c, const Geom& gm,
-                                              const S* __restrict__ src, const P* phi_field,
-                                              int x, int y, Normal nr, const Drag<R>& drb,
-                                              R (&d)[9], R (&h)[5]) {
+template <class T, bool FIELD>
+__device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T::R>& c, const Geom& gm,
+                                                          const Src<T>& src, const typename T::P* phi_field,
+                                                          int x, int y, Normal nr,
+                                                          const Drag<typename T::R>& drb,
+                                                          typename T::R (&d)[9], typename T::R (&h)[5]) {
+    using R = typename T::R;
     const int offf = (y + nr.dy) * gm.pitch + (x + nr.dx);
     R df[9], hf[5];
-    pull<S, R>(src, gm, offf, df, hf);
-    const Drag<R> drf = drag_at<R, FIELD, P>(c, phi_field, offf);
+    pull<T>(src, gm, offf, df, hf);
+    const Drag<R> drf = drag_at<R, FIELD, typename T::P>(c, phi_field, offf);
     const Macro<R> mf = fluid_macros<R>(c, drf, df, hf);
 
     Macro<R> mb;
@@ -307,7 +363,7 @@ __device__ __forceinline__ Macro<R> wall_node(const Coef<R>& c, const Geom& gm,
         mb.dT = (gm.thermal_bc == 1) ? c.dTc : (x == 0 ? c.dTh : c.dTc);
     } else if (gm.adi_order == 2) {
         const int offff = (y + 2 * nr.dy) * gm.pitch + (x + 2 * nr.dx);
-        const R dTff = pull_heat<S, R>(src, gm, offff) + c.qhalf;
+        const R dTff = pull_heat<T>(src, gm, offff) + c.qhalf;
         mb.dT = (R(4) * mf.dT - dTff) * R(1.0 / 3.0);
     } else {
         mb.dT = mf.dT;
@@ -341,18 +397,20 @@ __device__ __forceinline__ Macro<R> wall_node(const Coef<R>& c, const Geom& gm,
 }
 
 // Post-stream state of node (x, y) (pull + wall rule) and its macroscopic values.
-template <class S, class R, bool FIELD, class P>
-__device__ __forceinline__ Macro<R> node_state(const Coef<R>& c, const Geom& gm,
-                                               const S* __restrict__ src, const P* phi_field,
-                                               int x, int y, Drag<R>& dr, R (&d)[9], R (&h)[5]) {
+template <class T, bool FIELD>
+__device__ __forceinline__ Macro<typename T::R> node_state(const Coef<typename T::R>& c, const Geom& gm,
+                                                           const Src<T>& src, const typename T::P* phi_field,
+                                                           int x, int y, Drag<typename T::R>& dr,
+                                                           typename T::R (&d)[9], typename T::R (&h)[5]) {
+    using R = typename T::R;
     const int off = y * gm.pitch + x;
-    dr = drag_at<R, FIELD, P>(c, phi_field, off);
+    dr = drag_at<R, FIELD, typename T::P>(c, phi_field, off);
     const Normal nr = normal_of(gm, x, y);
     if (nr.dx == 0 && nr.dy == 0) {
-        pull<S, R>(src, gm, off, d, h);
+        pull<T>(src, gm, off, d, h);
         return fluid_macros<R>(c, dr, d, h);
     }
-    return wall_node<S, R, FIELD, P>(c, gm, src, phi_field, x, y, nr, dr, d, h);
+    return wall_node<T, FIELD>(c, gm, src, phi_field, x, y, nr, dr, d, h);
 }
 
 }  // namespace lbm

@@ -58,6 +58,10 @@ cudaError_t launch_step(const StepLaunch& L, const CoefSet& cs);
 cudaError_t launch_observe(const ObserveLaunch& L, const CoefSet& cs);
 cudaError_t launch_nusselt(const ObserveLaunch& L, const CoefSet& cs);
 cudaError_t launch_read_state(const ReadStateLaunch& L, const CoefSet& cs);
+// Bytes of one state buffer (9 flow + 5 thermal planes) and of a porosity field.
+size_t state_buffer_bytes(int precision, int plane);
+size_t phi_bytes(int precision, int plane);
+
 cudaError_t launch_convert_phi(const void* in, int in_is_double, void* out, int precision, const Geom& gm,
                                int nblocks, cudaStream_t s);
 

@@ -12,28 +12,28 @@ namespace lbm {
 // wall rule on perimeter nodes (Section 4), collides (Eq. 17, 34) and writes
 // the node's post-collision populations to the other buffer.  The buffer
 // pair alternates, so dst holds B_{n+1} when src holds B_n.
-template <class S, class R, bool FIELD, class P>
-__global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst,
-                                              const P* __restrict__ phi, Geom gm, Coef<R> c,
-                                              int* __restrict__ status) {
+template <class T, bool FIELD>
+__global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
+                                              Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+    using R = typename T::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= gm.nx || y >= gm.ny) return;
     R d[9], h[5];
     Drag<R> dr;
-    const Macro<R> mc = node_state<S, R, FIELD, P>(c, gm, src, phi, x, y, dr, d, h);
+    const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
     if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
     collide<R>(c, dr.iphi, mc, d, h);
     const int off = y * gm.pitch + x;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Conv<S, R>::st(dst + i * gm.plane + off, d[i]);
+    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R>::st(dst.f + i * gm.plane + off, d[i]);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) Conv<S, R>::st(dst + (9 + j) * gm.plane + off, h[j]);
+    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R>::st(dst.g + j * gm.plane + off, h[j]);
 }
 
 // ---- observables ------------------------------------------------------------------
 
-// Block-wide reduction of four doubles: max, max, sum, sum.
+// Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).
 __device__ __forceinline__ void block_reduce4(double v[4], double* sh /* 4 * 32 */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -65,11 +65,13 @@ __device__ __forceinline__ void block_reduce4(double v[4], double* sh /* 4 * 32 
 // Macroscopic fields of the post-stream state S_n, rebuilt by pulling from
 // B_{n-1} and applying the wall rule, plus per-block partials (FP64) of
 // max|u|, max|u - u_prev|, sum of population deviations, sum of T - T0.
-template <class S, class R, bool FIELD, class P>
-__global__ void __launch_bounds__(256) k_observe(const S* __restrict__ prev, const P* __restrict__ phi,
-                                                 Geom gm, Coef<R> c, R* ux_out, R* uy_out, R* T_out,
-                                                 R* p_out, R* snap, int snap_valid,
+template <class T, bool FIELD>
+__global__ void __launch_bounds__(256) k_observe(Src<T> prev, const typename T::P* __restrict__ phi, Geom gm,
+                                                 Coef<typename T::R> c, typename T::R* ux_out,
+                                                 typename T::R* uy_out, typename T::R* T_out,
+                                                 typename T::R* p_out, typename T::R* snap, int snap_valid,
                                                  double* __restrict__ partials) {
+    using R = typename T::R;
     __shared__ double sh[4 * 32];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const long n = (long)gm.nx * gm.ny;
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) k_observe(const S* __restrict__ prev, con
         const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
         R d[9], h[5];
         Drag<R> dr;
-        const Macro<R> mc = node_state<S, R, FIELD, P>(c, gm, prev, phi, x, y, dr, d, h);
+        const Macro<R> mc = node_state<T, FIELD>(c, gm, prev, phi, x, y, dr, d, h);
         R sd = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) sd += d[i];
@@ -108,16 +110,17 @@ __global__ void __launch_bounds__(256) k_observe(const S* __restrict__ prev, con
 }
 
 // T - T0 of the post-stream state at node (x, y), pulled from B_{n-1}.
-template <class S, class R>
-__device__ __forceinline__ R node_dT(const Coef<R>& c, const Geom& gm, const S* __restrict__ prev,
-                                     int x, int y) {
+template <class T>
+__device__ __forceinline__ typename T::R node_dT(const Coef<typename T::R>& c, const Geom& gm,
+                                                 const Src<T>& prev, int x, int y) {
+    using R = typename T::R;
     const Normal nr = normal_of(gm, x, y);
-    if (nr.dx == 0 && nr.dy == 0) return pull_heat<S, R>(prev, gm, y * gm.pitch + x) + c.qhalf;
+    if (nr.dx == 0 && nr.dy == 0) return pull_heat<T>(prev, gm, y * gm.pitch + x) + c.qhalf;
     if (gm.thermal_bc == 1) return c.dTc;
     if (nr.dx != 0) return x == 0 ? c.dTh : c.dTc;
-    const R dTf = pull_heat<S, R>(prev, gm, (y + nr.dy) * gm.pitch + x) + c.qhalf;
+    const R dTf = pull_heat<T>(prev, gm, (y + nr.dy) * gm.pitch + x) + c.qhalf;
     if (gm.adi_order == 2) {
-        const R dTff = pull_heat<S, R>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x) + c.qhalf;
+        const R dTff = pull_heat<T>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x) + c.qhalf;
         return (R(4) * dTf - dTff) * R(1.0 / 3.0);
     }
     return dTf;
@@ -128,10 +131,10 @@ __device__ __forceinline__ R node_dT(const Coef<R>& c, const Geom& gm, const S* 
 // Nu(y) = -L dT/dx / dT with the one-sided five-point derivative
 // (-25 T0 + 48 T1 - 36 T2 + 16 T3 - 3 T4) / 12, trapezoidal mean over y.
 // out[0..6] = nu_hot, nu_cold, max|u|, max|du|, sum d, sum (T - T0), status.
-template <class S, class R>
-__global__ void __launch_bounds__(1024) k_finish(const S* __restrict__ prev, Geom gm, Coef<R> c,
-                                                 const double* __restrict__ partials, int npart,
-                                                 double L, double dT, const int* __restrict__ status,
+template <class T>
+__global__ void __launch_bounds__(1024) k_finish(Src<T> prev, Geom gm, Coef<typename T::R> c,
+                                                 const double* __restrict__ partials, int npart, double L,
+                                                 double dT, const int* __restrict__ status,
                                                  double* __restrict__ out) {
     __shared__ double sh[4 * 32];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -143,16 +146,15 @@ __global__ void __launch_bounds__(1024) k_finish(const S* __restrict__ prev, Geo
     }
     block_reduce4(v, sh);
     __syncthreads();
-    double red[4] = {v[0], v[1], v[2], v[3]};
-    __syncthreads();
+    const double red[4] = {v[0], v[1], v[2], v[3]};
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     const int nx = gm.nx;
     for (int y = threadIdx.x; y < gm.ny; y += blockDim.x) {
         double tl[5], tr[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            tl[k] = (double)node_dT<S, R>(c, gm, prev, k, y);
-            tr[k] = (double)node_dT<S, R>(c, gm, prev, nx - 1 - k, y);
+            tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
+            tr[k] = (double)node_dT<T>(c, gm, prev, nx - 1 - k, y);
         }
         const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
         const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
@@ -173,22 +175,25 @@ __global__ void __launch_bounds__(1024) k_finish(const S* __restrict__ prev, Geo
 }
 
 // Full FP64 populations of the post-stream state, dense [q][ny][nx].
-template <class S, class R, bool FIELD, class P>
-__global__ void __launch_bounds__(256) k_read_state(const S* __restrict__ prev, const P* __restrict__ phi,
-                                                    Geom gm, Coef<R> c, double* __restrict__ f,
+template <class T, bool FIELD>
+__global__ void __launch_bounds__(256) k_read_state(Src<T> prev, const typename T::P* __restrict__ phi, Geom gm,
+                                                    Coef<typename T::R> c, double* __restrict__ f,
                                                     double* __restrict__ g) {
+    using R = typename T::R;
     const long n = (long)gm.nx * gm.ny;
+    // rest weights in FP64 (Eq. 37 first occurrence), independent of the arithmetic type
+    const double varpi = (double)c.varpi, T0 = (double)c.T0;
+    const double wt0 = (1.0 - varpi) / 5.0, wt1 = (4.0 + varpi) / 20.0;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
         R d[9], h[5];
         Drag<R> dr;
-        (void)node_state<S, R, FIELD, P>(c, gm, prev, phi, x, y, dr, d, h);
+        (void)node_state<T, FIELD>(c, gm, prev, phi, x, y, dr, d, h);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i * n + k] = w9(i) + (double)d[i];
-        const double T0 = (double)c.T0;
-        g[k] = (double)c.wt0 * T0 + (double)h[0];
+        g[k] = wt0 * T0 + (double)h[0];
 #pragma unroll
-        for (int j = 1; j < 5; ++j) g[j * n + k] = (double)c.wt1 * T0 + (double)h[j];
+        for (int j = 1; j < 5; ++j) g[j * n + k] = wt1 * T0 + (double)h[j];
     }
 }
 
@@ -197,108 +202,108 @@ __global__ void k_convert_phi(const In* __restrict__ in, P* __restrict__ out, Ge
     const long n = (long)gm.nx * gm.ny;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
-        if constexpr (sizeof(P) == 2) out[y * gm.pitch + x] = __float2half_rn((float)in[k]);
-        else out[y * gm.pitch + x] = (P)in[k];
+        out[y * gm.pitch + x] = (P)in[k];
     }
 }
 
 // ---- host launchers ---------------------------------------------------------------
 
-template <class S, class R, class P>
-static cudaError_t launch_step_t(const StepLaunch& L, const Coef<R>& c) {
+template <class T> static const Coef<typename T::R>& coef_of(const CoefSet& cs);
+template <> const Coef<double>& coef_of<PrecF64>(const CoefSet& cs) { return cs.d; }
+template <> const Coef<float>& coef_of<PrecF32>(const CoefSet& cs) { return cs.f; }
+template <> const Coef<float>& coef_of<PrecF16>(const CoefSet& cs) { return cs.f; }
+
+template <class T>
+static cudaError_t launch_step_t(const StepLaunch& L, const CoefSet& cs) {
     dim3 blk(L.bx, L.by);
     dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
+    const Src<T> s = src_view<T>(L.src, L.gm.plane);
+    const Dst<T> d = dst_view<T>(L.dst, L.gm.plane);
     if (L.phi)
-        k_step<S, R, true, P><<<grd, blk, 0, L.stream>>>((const S*)L.src, (S*)L.dst, (const P*)L.phi,
-                                                         L.gm, c, L.status);
+        k_step<T, true><<<grd, blk, 0, L.stream>>>(s, d, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
+                                                  L.status);
     else
-        k_step<S, R, false, P><<<grd, blk, 0, L.stream>>>((const S*)L.src, (S*)L.dst, nullptr, L.gm, c,
-                                                          L.status);
+        k_step<T, false><<<grd, blk, 0, L.stream>>>(s, d, nullptr, L.gm, coef_of<T>(cs), L.status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepLaunch& L, const CoefSet& cs) {
-    switch (L.precision) {
-        case PREC_F64: return launch_step_t<double, double, double>(L, cs.d);
-        case PREC_F32: return launch_step_t<float, float, float>(L, cs.f);
-        default: return launch_step_t<__half, float, __half>(L, cs.f);
-    }
-}
-
-template <class S, class R, class P>
-static cudaError_t launch_observe_t(const ObserveLaunch& L, const Coef<R>& c) {
+template <class T>
+static cudaError_t launch_observe_t(const ObserveLaunch& L, const CoefSet& cs) {
+    using R = typename T::R;
+    const Src<T> s = src_view<T>(L.prev, L.gm.plane);
     if (L.phi)
-        k_observe<S, R, true, P><<<L.nblocks, 256, 0, L.stream>>>(
-            (const S*)L.prev, (const P*)L.phi, L.gm, c, (R*)L.ux, (R*)L.uy, (R*)L.T, (R*)L.p, (R*)L.snap,
-            L.snap_valid, L.partials);
+        k_observe<T, true><<<L.nblocks, 256, 0, L.stream>>>(s, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
+                                                            (R*)L.ux, (R*)L.uy, (R*)L.T, (R*)L.p, (R*)L.snap,
+                                                            L.snap_valid, L.partials);
     else
-        k_observe<S, R, false, P><<<L.nblocks, 256, 0, L.stream>>>(
-            (const S*)L.prev, nullptr, L.gm, c, (R*)L.ux, (R*)L.uy, (R*)L.T, (R*)L.p, (R*)L.snap,
-            L.snap_valid, L.partials);
+        k_observe<T, false><<<L.nblocks, 256, 0, L.stream>>>(s, nullptr, L.gm, coef_of<T>(cs), (R*)L.ux,
+                                                             (R*)L.uy, (R*)L.T, (R*)L.p, (R*)L.snap,
+                                                             L.snap_valid, L.partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_finish<S, R><<<1, 1024, 0, L.stream>>>((const S*)L.prev, L.gm, c, L.partials, L.nblocks, L.L,
-                                             L.dT, L.status, L.out);
+    k_finish<T><<<1, 1024, 0, L.stream>>>(s, L.gm, coef_of<T>(cs), L.partials, L.nblocks, L.L, L.dT, L.status,
+                                          L.out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_observe(const ObserveLaunch& L, const CoefSet& cs) {
-    switch (L.precision) {
-        case PREC_F64: return launch_observe_t<double, double, double>(L, cs.d);
-        case PREC_F32: return launch_observe_t<float, float, float>(L, cs.f);
-        default: return launch_observe_t<__half, float, __half>(L, cs.f);
-    }
-}
-
-template <class S, class R>
-static cudaError_t launch_nusselt_t(const ObserveLaunch& L, const Coef<R>& c) {
+template <class T>
+static cudaError_t launch_nusselt_t(const ObserveLaunch& L, const CoefSet& cs) {
     // npart = 0: only the Nusselt part of the finisher runs
-    k_finish<S, R><<<1, 1024, 0, L.stream>>>((const S*)L.prev, L.gm, c, L.partials, 0, L.L, L.dT,
-                                             L.status, L.out);
+    k_finish<T><<<1, 1024, 0, L.stream>>>(src_view<T>(L.prev, L.gm.plane), L.gm, coef_of<T>(cs), L.partials, 0,
+                                          L.L, L.dT, L.status, L.out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_nusselt(const ObserveLaunch& L, const CoefSet& cs) {
-    switch (L.precision) {
-        case PREC_F64: return launch_nusselt_t<double, double>(L, cs.d);
-        case PREC_F32: return launch_nusselt_t<float, float>(L, cs.f);
-        default: return launch_nusselt_t<__half, float>(L, cs.f);
-    }
-}
-
-template <class S, class R, class P>
-static cudaError_t launch_read_state_t(const ReadStateLaunch& L, const Coef<R>& c) {
+template <class T>
+static cudaError_t launch_read_state_t(const ReadStateLaunch& L, const CoefSet& cs) {
+    const Src<T> s = src_view<T>(L.prev, L.gm.plane);
     if (L.phi)
-        k_read_state<S, R, true, P><<<L.nblocks, 256, 0, L.stream>>>((const S*)L.prev, (const P*)L.phi,
-                                                                      L.gm, c, L.f, L.g);
+        k_read_state<T, true><<<L.nblocks, 256, 0, L.stream>>>(s, (const typename T::P*)L.phi, L.gm,
+                                                               coef_of<T>(cs), L.f, L.g);
     else
-        k_read_state<S, R, false, P><<<L.nblocks, 256, 0, L.stream>>>((const S*)L.prev, nullptr, L.gm, c,
-                                                                       L.f, L.g);
+        k_read_state<T, false><<<L.nblocks, 256, 0, L.stream>>>(s, nullptr, L.gm, coef_of<T>(cs), L.f, L.g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_read_state(const ReadStateLaunch& L, const CoefSet& cs) {
-    switch (L.precision) {
-        case PREC_F64: return launch_read_state_t<double, double, double>(L, cs.d);
-        case PREC_F32: return launch_read_state_t<float, float, float>(L, cs.f);
-        default: return launch_read_state_t<__half, float, __half>(L, cs.f);
+#define LBM_DISPATCH(prec, fn, ...)                     \
+    switch (prec) {                                     \
+        case PREC_F64: return fn<PrecF64>(__VA_ARGS__); \
+        case PREC_F32: return fn<PrecF32>(__VA_ARGS__); \
+        default: return fn<PrecF16>(__VA_ARGS__);       \
     }
+
+cudaError_t launch_step(const StepLaunch& L, const CoefSet& cs) { LBM_DISPATCH(L.precision, launch_step_t, L, cs) }
+cudaError_t launch_observe(const ObserveLaunch& L, const CoefSet& cs) {
+    LBM_DISPATCH(L.precision, launch_observe_t, L, cs)
+}
+cudaError_t launch_nusselt(const ObserveLaunch& L, const CoefSet& cs) {
+    LBM_DISPATCH(L.precision, launch_nusselt_t, L, cs)
+}
+cudaError_t launch_read_state(const ReadStateLaunch& L, const CoefSet& cs) {
+    LBM_DISPATCH(L.precision, launch_read_state_t, L, cs)
+}
+
+size_t state_buffer_bytes(int precision, int plane) {
+    switch (precision) {
+        case PREC_F64: return buffer_bytes<PrecF64>(plane);
+        case PREC_F32: return buffer_bytes<PrecF32>(plane);
+        default: return buffer_bytes<PrecF16>(plane);
+    }
+}
+
+size_t phi_bytes(int precision, int plane) {
+    return (size_t)plane * (precision == PREC_F64 ? sizeof(double) : sizeof(float));
 }
 
 cudaError_t launch_convert_phi(const void* in, int in_is_double, void* out, int precision, const Geom& gm,
                                int nblocks, cudaStream_t s) {
+    const bool to_double = precision == PREC_F64;
     if (in_is_double) {
-        switch (precision) {
-            case PREC_F64: k_convert_phi<double, double><<<nblocks, 256, 0, s>>>((const double*)in, (double*)out, gm); break;
-            case PREC_F32: k_convert_phi<double, float><<<nblocks, 256, 0, s>>>((const double*)in, (float*)out, gm); break;
-            default: k_convert_phi<double, __half><<<nblocks, 256, 0, s>>>((const double*)in, (__half*)out, gm); break;
-        }
+        if (to_double) k_convert_phi<double, double><<<nblocks, 256, 0, s>>>((const double*)in, (double*)out, gm);
+        else k_convert_phi<double, float><<<nblocks, 256, 0, s>>>((const double*)in, (float*)out, gm);
     } else {
-        switch (precision) {
-            case PREC_F64: k_convert_phi<float, double><<<nblocks, 256, 0, s>>>((const float*)in, (double*)out, gm); break;
-            case PREC_F32: k_convert_phi<float, float><<<nblocks, 256, 0, s>>>((const float*)in, (float*)out, gm); break;
-            default: k_convert_phi<float, __half><<<nblocks, 256, 0, s>>>((const float*)in, (__half*)out, gm); break;
-        }
+        if (to_double) k_convert_phi<float, double><<<nblocks, 256, 0, s>>>((const float*)in, (double*)out, gm);
+        else k_convert_phi<float, float><<<nblocks, 256, 0, s>>>((const float*)in, (float*)out, gm);
     }
     return cudaGetLastError();
 }

@@ -3,10 +3,15 @@
 Tolerances (max over the lattice):
   FP64 path:   populations 1e-13 absolute after one step; fields 1e-10
                relative (velocity to max|u|, temperature to dT), Nu 1e-10.
-  FP32 path:   one-step populations 2e-7 absolute (FP32 rounding of O(1e-2)
-               deviations plus FP32 arithmetic); long runs per field below.
-  FP16 store:  one-step populations 3e-5 absolute (half rounding of the
-               deviations); long runs per field below.
+  FP32 path:   one-step populations 2e-7 absolute: stored deviations stay
+               below 0.5 in magnitude (the largest is w~_0 (T_h - T0) = 0.3 at
+               the hot wall), FP32 rounds them to within 3e-8, and the step's
+               FP32 arithmetic adds a few more roundings of that size.
+  FP16 flow:   flow deviations stay below 0.0625 (|u| <~ 0.05 here), where
+               half precision rounds to within 2^-16 = 1.5e-5: one-step flow
+               populations 3e-5; thermal planes are FP32 (2e-7).
+  Long runs (2e4 steps) accumulate rounding; the per-field bounds below are
+  the measured errors with a margin of about three.
 """
 import numpy as np
 import pytest
@@ -49,9 +54,10 @@ def field_errors(obs, o):
 
 # ---- one-step map, every population, several tiles and ragged tails ----------
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 2e-7), ("f16", 3e-5)])
+@pytest.mark.parametrize("precision,tol_f,tol_g", [("f64", 1e-13, 1e-13), ("f32", 2e-7, 2e-7),
+                                                  ("f16", 3e-5, 2e-7)])
 @pytest.mark.parametrize("shape", [(17, 13), (64, 64), (131, 70), (300, 257)])
-def test_one_step_populations(precision, tol, shape, nthreads):
+def test_one_step_populations(precision, tol_f, tol_g, shape, nthreads):
     nx, ny = shape
     Ra, Da, phi = 1e5, 1e-2, 0.6
     cav = cavity(nx, ny, Ra=Ra, Da=Da, phi=phi, precision=precision)
@@ -67,7 +73,7 @@ def test_one_step_populations(precision, tol, shape, nthreads):
         fo, go = o.state()
         ef = np.abs(np_(f1) - fo).max()
         eg = np.abs(np_(g1) - go).max()
-        assert ef < tol and eg < tol, (n, ef, eg)
+        assert ef < tol_f and eg < tol_g, (n, ef, eg)
     cav.close()
 
 
@@ -108,8 +114,8 @@ class _Snap:
 
 @pytest.mark.parametrize("precision,tol_u,tol_T,tol_nu", [
     ("f64", 1e-10, 1e-10, 1e-10),
-    ("f32", 2e-4, 2e-5, 2e-4),
-    ("f16", 2e-2, 2e-3, 2e-2),
+    ("f32", 2e-4, 1e-4, 1e-4),
+    ("f16", 5e-3, 1e-3, 1e-3),
 ])
 def test_config1_fields_and_nusselt(oracle_c1, precision, tol_u, tol_T, tol_nu):
     lat = derive(64, 64, Ra=1e4, Da=1e-2, phi=0.6)
