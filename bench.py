@@ -38,8 +38,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "coupled MLUPS & % HBM roofline, FP32 vs FP64 at stated Nu error; adjoint MLUPS"
-BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4, "f16": 28 * 2}
-DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-arith"}
+# every population read once and written once: FP64 14 x 8 B, FP32 14 x 4 B,
+# FP16 variant 9 x 2 B (flow) + 5 x 4 B (thermal), each way
+BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4, "f16": 2 * (9 * 2 + 5 * 4)}
+DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16 flow + f32 thermal storage, f32 arithmetic"}
 
 
 def parse():

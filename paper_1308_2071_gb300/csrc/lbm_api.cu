@@ -14,14 +14,9 @@ using namespace lbm;
 
 namespace {
 
-constexpr int kGraphSteps = 64;      // steps per captured graph (even: keeps buffer parity)
-constexpr int kReduceBlocks = 1216;  // 152 SMs x 8; fixed so FP64 sums are reproducible
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: keeps buffer parity)
 
 thread_local std::string g_init_error;
-
-struct Derived {
-    double L, tau_nu, tau_T, nu, gbeta, K, Fphi, T0, dT;
-};
 
 }  // namespace
 
@@ -150,6 +145,34 @@ void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
     }
 }
 
+}  // namespace
+
+namespace lbm {
+void set_global_error(const std::string& msg) { g_init_error = msg; }
+
+int setup_lattice(const lbm_params* p, Derived* dv, CoefSet* cs, Geom* gm, std::string* why) {
+    int rc = derive(p, dv, why);
+    if (rc != LBM_OK) return rc;
+    // row pitch in elements: rows of the flow planes and of the thermal planes
+    // both start on 128-byte boundaries (FP64: 16, FP32: 32, FP16 flow: 64)
+    const int align = p->precision == LBM_F64 ? 16 : (p->precision == LBM_F32 ? 32 : 64);
+    const long pitch = ((long)p->nx + align - 1) / align * align;
+    const long plane = pitch * (long)p->ny;
+    if (plane * NPOP >= (1L << 31)) return *why = "lattice too large for 32-bit offsets", LBM_ERR_ARG;
+    gm->nx = p->nx;
+    gm->ny = p->ny;
+    gm->pitch = (int)pitch;
+    gm->plane = (int)plane;
+    gm->thermal_bc = p->thermal_bc;
+    gm->adi_order = p->adiabatic_order;
+    fill_coef<double>(p, *dv, &cs->d);
+    fill_coef<float>(p, *dv, &cs->f);
+    return LBM_OK;
+}
+}  // namespace lbm
+
+namespace {
+
 void free_handle(lbm_handle h) {
     if (!h) return;
     for (int k = 0; k < 2; ++k) {
@@ -257,32 +280,16 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
-    Derived dv;
-    std::string why;
-    int rc = derive(p, &dv, &why);
-    if (rc != LBM_OK) return fail(nullptr, rc, why);
-
     lbm_handle h = new lbm_handle_s();
-    h->p = *p;
-    h->dv = dv;
-    h->precision = p->precision;
-    // row pitch in elements: rows of the flow planes and of the thermal planes
-    // both start on 128-byte boundaries (FP64: 16, FP32: 32, FP16 flow: 64)
-    const int align = p->precision == LBM_F64 ? 16 : (p->precision == LBM_F32 ? 32 : 64);
-    const long pitch = ((long)p->nx + align - 1) / align * align;
-    const long plane = pitch * (long)p->ny;
-    if (plane * NPOP >= (1L << 31)) {
+    std::string why;
+    int rc = setup_lattice(p, &h->dv, &h->coef, &h->gm, &why);
+    if (rc != LBM_OK) {
         delete h;
-        return fail(nullptr, LBM_ERR_ARG, "lattice too large for 32-bit offsets");
+        return fail(nullptr, rc, why);
     }
-    h->gm.nx = p->nx;
-    h->gm.ny = p->ny;
-    h->gm.pitch = (int)pitch;
-    h->gm.plane = (int)plane;
-    h->gm.thermal_bc = p->thermal_bc;
-    h->gm.adi_order = p->adiabatic_order;
-    fill_coef<double>(p, dv, &h->coef.d);
-    fill_coef<float>(p, dv, &h->coef.f);
+    h->p = *p;
+    h->precision = p->precision;
+    const long plane = h->gm.plane;
     h->bx = p->block_x > 0 ? p->block_x : (p->nx <= 64 ? 64 : 128);
     h->by = p->block_y > 0 ? p->block_y : 256 / h->bx;
     if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0) {
@@ -455,15 +462,6 @@ int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev) {
     CK(h, launch_read_state(L, h->coef));
     return LBM_OK;
 }
-
-namespace {
-struct CkptHeader {
-    char magic[8];
-    int version, nx, ny, precision;
-    long t;
-    long payload;  // bytes of buffer data that follow
-};
-}  // namespace
 
 int lbm_checkpoint_size(lbm_handle h, size_t* bytes) {
     if (!h || !bytes) return fail(h, LBM_ERR_ARG, "handle and bytes are required");

@@ -5,9 +5,35 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Lattice parameters derived from lbm_params (Section 4 set-up).
+struct Derived {
+    double L, tau_nu, tau_T, nu, gbeta, K, Fphi, T0, dT;
+};
+
+// Validates p and fills the derived parameters, the coefficients in both
+// arithmetic types and the geometry; returns LBM_OK or LBM_ERR_ARG with *why.
+int setup_lattice(const lbm_params* p, Derived* dv, struct CoefSet* cs, Geom* gm, std::string* why);
+
+// Header of a checkpoint (lbm_save / lbm_load); the payload that follows is
+// the two state buffers, B_{n-1} then B_n.
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, precision;
+    long t;
+    long payload;
+};
+
+// Error text returned by lbm_last_error(NULL) (calls without a handle).
+void set_global_error(const std::string& msg);
+
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8; fixed so FP64 sums are reproducible
 
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2 };
 

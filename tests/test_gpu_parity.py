@@ -77,15 +77,16 @@ def test_one_step_populations(precision, tol_f, tol_g, shape, nthreads):
     cav.close()
 
 
-def test_initial_state_matches_oracle():
-    for prec in ("f64", "f32", "f16"):
-        cav = cavity(20, 16, Ra=1e4, Da=1e-2, phi=0.6, precision=prec)
-        o = Oracle(derive(20, 16, Ra=1e4, Da=1e-2, phi=0.6))
-        f, g = cav.read_state()
-        fo, go = o.state()
-        assert np.abs(np_(f) - fo).max() < 1e-15
-        assert np.abs(np_(g) - go).max() < 1e-15
-        cav.close()
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-15), ("f32", 2e-7), ("f16", 2e-7)])
+def test_initial_state_matches_oracle(precision, tol):
+    # the wall rule applied to the rest state (FP32 paths round w~_j (T_w - T0))
+    cav = cavity(20, 16, Ra=1e4, Da=1e-2, phi=0.6, precision=precision)
+    o = Oracle(derive(20, 16, Ra=1e4, Da=1e-2, phi=0.6))
+    f, g = cav.read_state()
+    fo, go = o.state()
+    assert np.abs(np_(f) - fo).max() < tol
+    assert np.abs(np_(g) - go).max() < tol
+    cav.close()
 
 
 # ---- long runs of the cavity of config 1 ---------------------------------------------
