@@ -149,6 +149,33 @@ int lbm_checkpoint_size(lbm_handle h, size_t* bytes);
 int lbm_save(lbm_handle h, void* host, size_t bytes);
 int lbm_load(lbm_handle h, const void* host, size_t bytes);
 
+/* Observables of a saved lattice, computed without allocating any memory.
+ * For callers that may not allocate device memory on their call path: a
+ * framework's custom operator whose device memory belongs to the framework's
+ * own allocator or to a fixed budget, or a monitoring stage that runs between
+ * latency-critical GPU work, where a cudaMalloc would synchronise the device.
+ * The caller keeps a checkpoint (the bytes lbm_save writes: header, then the
+ * two state buffers) in its own device memory at ckpt_dev, `bytes` long, and
+ * passes the lbm_params it was made with.  The function computes what
+ * lbm_observables computes for that state, except the residual (reported as
+ * 0), writes *out (host) and, for each non-NULL pointer, the field (ny*nx
+ * device values, double for LBM_F64, float otherwise); the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default) and synchronised before
+ * the call returns.  The paper has no counterpart to this call.
+ * Scratch: one static device array of 38,984 bytes (the FP64 partial sums of
+ * the fixed 1216-block reduction grid, the result, and a status word), which
+ * every device that loads the library holds until the process exits; any
+ * lattice that lbm_init accepts uses the same grid.  The first call on a
+ * device looks up that array's device address once, with the device current:
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the previous call's contents (the status word is cleared on
+ * entry), so calls that overlap on the GPU race: serialise them.
+ * Errors: LBM_ERR_ARG (invalid parameters, use_phi_field set, a lattice
+ * beyond 32-bit offsets, a buffer smaller than the lattice needs, a header
+ * that does not match p), LBM_ERR_CUDA; lbm_last_error(NULL) describes it. */
+int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t bytes, void* stream,
+                            lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev, void* p_dev);
+
 /* Current time step count and divergence status (synchronises the stream). */
 int lbm_query(lbm_handle h, long* t, int* status);
 

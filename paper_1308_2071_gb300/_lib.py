@@ -54,6 +54,8 @@ SIGNATURES = [
     ("lbm_checkpoint_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("lbm_save", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("lbm_load", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("lbm_observables_noalloc", C.c_int, [C.POINTER(Params), C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(Obs),
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_query", C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     ("lbm_destroy", C.c_int, [C.c_void_p]),
     ("lbm_last_error", C.c_char_p, [C.c_void_p]),
