@@ -211,6 +211,40 @@ def e2e_leg(n, precision, steps):
                 seconds=round(t1 - t0, 3))
 
 
+def batched_leg(steps, warmup, ncav=256, seed=2071):
+    """Batched sweep: ncav cavities of uneven size (64^2..512^2), log-uniform Ra
+    and Da, uniform porosity (seeded draws), FP32, one persistent
+    graph-captured launch per call, autotuned tile shape."""
+    import torch
+
+    from paper_1308_2071_gb300 import Batch
+    from paper_1308_2071_gb300.inputs import cavity_sweep
+
+    cavs = cavity_sweep(ncav, seed=seed)
+    nodes = sum(c["nx"] * c["ny"] for c in cavs)
+    b = Batch(cavs, precision="f32")
+    cache = os.path.join(ROOT, "paper_1308_2071_gb300", "_build", "tune_cache.txt")
+    tw, th, bps = b.tune(cache)
+    b.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc, st = b.status()
+    q = b.query()
+    b.close()
+    peak, _ = load_peaks()
+    gbs = nodes * BYTES_PER_NODE["f32"] / (ms * 1e-3 / steps) / 1e9
+    return dict(cavities=ncav, nodes=nodes, steps=steps, mlups=round(nodes * steps / (ms * 1e-3) / 1e6, 2),
+                hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / peak, 4), tile=[tw, th], blocks_per_sm=bps,
+                blocks=q["nblocks"], tiles=q["ntiles"], launches=1, diverged=int(st.sum()),
+                status=int(rc), sizes="U{64..512} square, seed %d" % seed)
+
+
 def cpu_leg(n, seconds, warmup=1, max_steps=None):
     """The FP64 oracle as it stands, on every host core, on a bounded number of
     steps of the same lattice; returns (MLUPS, threads, steps, seconds)."""
@@ -294,6 +328,7 @@ def main():
         variants["nu_rel_err_f16_vs_f64"] = abs(variants["f16"]["nu_hot"] - nu64) / abs(nu64)
         line["variants"] = variants
         line["e2e"] = e2e_leg(a.size, a.precision, min(a.steps, 1000))
+        line["batched"] = batched_leg(min(a.steps, 1000), 8)
         mlc, threads, k, dt = cpu_leg(a.size, a.cpu_seconds)
         line["cpu_baseline"] = dict(value=round(mlc, 3), unit="MLUPS", cores=threads, kind="oracle",
                                     sample=f"{k} steps of the {a.size}^2 lattice, FP64 oracle, {dt:.1f} s")

@@ -176,6 +176,47 @@ int lbm_load(lbm_handle h, const void* host, size_t bytes);
 int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t bytes, void* stream,
                             lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev, void* p_dev);
 
+/* ---- batched sweep ---------------------------------------------------------
+ * Many independent cavities (each its own nx, ny, Ra, Da, porosity, ...; one
+ * precision, LBM_F32 or LBM_F64, uniform porosity) advanced together: every
+ * lbm_batch_step() is ONE persistent cooperative kernel launch that runs all
+ * requested steps of all cavities (blocks walk a tile list that covers every
+ * cavity; a bounded grid-wide barrier separates the steps), captured into a
+ * CUDA graph on first use and replayed.  Per node it runs the same code as
+ * lbm_step, so each cavity evolves exactly as it would alone. */
+typedef struct lbm_batch_s* lbm_batch;
+
+/* p: ncav parameter sets (host); same precision in all.  Initial state as in
+ * lbm_init.  Errors: LBM_ERR_ARG (with the cavity index in the message),
+ * LBM_ERR_CUDA. */
+int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out);
+/* Advances every cavity by nsteps (asynchronous, one launch). */
+int lbm_batch_step(lbm_batch b, long nsteps);
+/* Mean Nusselt numbers (Eq. 38) of every cavity into host arrays of ncav
+ * doubles (either may be NULL); synchronises. */
+int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold);
+/* Per-cavity divergence status into status[ncav] (may be NULL); returns
+ * LBM_ERR_TIMEOUT if a grid-barrier wait ran out in any step since the last
+ * lbm_batch_set_wait_limit (the lattice is then incomplete), LBM_ERR_DIVERGED
+ * if any cavity diverged, else LBM_OK.  Synchronises. */
+int lbm_batch_status(lbm_batch b, int* status);
+/* FP64 post-stream populations of cavity cav (as lbm_read_state). */
+int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev);
+/* Upper bound on the polls (about 0.1 us or more each) a block spends at the
+ * grid barrier before it records LBM_ERR_TIMEOUT and leaves the kernel;
+ * default 2e7.  Also clears a previous timeout. */
+int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
+/* Autotuner: times candidate tile shapes (tile_w x tile_h nodes) and blocks
+ * per SM on this batch, keeps the fastest, and records it in a text cache
+ * (one line per device, precision and batch shape) at cache_path (NULL: no
+ * cache); a cached entry is reused without timing.  Tuning advances the
+ * lattices, so the batch is reset to t = 0 afterwards.  Outputs may be NULL. */
+int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm);
+/* Steps taken, number of tiles and blocks of the persistent launch. */
+int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks);
+int lbm_batch_destroy(lbm_batch b);
+const char* lbm_batch_last_error(lbm_batch b);
+
 /* Current time step count and divergence status (synchronises the stream). */
 int lbm_query(lbm_handle h, long* t, int* status);
 

@@ -7,11 +7,11 @@ Python binding.  Importing the package loads nothing; the first use of the
 library raises if liblbm.so has not been built.
 """
 
-__all__ = ["Cavity", "make_params", "build"]
+__all__ = ["Cavity", "Batch", "make_params", "build"]
 
 
 def __getattr__(name):
-    if name in ("Cavity", "make_params"):
+    if name in ("Cavity", "Batch", "make_params"):
         from . import lbm
         return getattr(lbm, name)
     if name == "build":

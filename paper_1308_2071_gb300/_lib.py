@@ -56,6 +56,17 @@ SIGNATURES = [
     ("lbm_load", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("lbm_observables_noalloc", C.c_int, [C.POINTER(Params), C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(Obs),
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lbm_batch_init", C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("lbm_batch_step", C.c_int, [C.c_void_p, C.c_long]),
+    ("lbm_batch_nusselt", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lbm_batch_status", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("lbm_batch_read_state", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("lbm_batch_set_wait_limit", C.c_int, [C.c_void_p, C.c_longlong]),
+    ("lbm_batch_tune", C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
+    ("lbm_batch_query", C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("lbm_batch_destroy", C.c_int, [C.c_void_p]),
+    ("lbm_batch_last_error", C.c_char_p, [C.c_void_p]),
     ("lbm_query", C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     ("lbm_destroy", C.c_int, [C.c_void_p]),
     ("lbm_last_error", C.c_char_p, [C.c_void_p]),
@@ -80,7 +91,7 @@ def load(path: str | None = None):
     return _lib
 
 
-def check(rc: int, handle=None):
+def check(rc: int, handle=None, batch=None):
     if rc != LBM_OK:
-        msg = load().lbm_last_error(handle)
+        msg = load().lbm_batch_last_error(batch) if batch is not None else load().lbm_last_error(handle)
         raise LbmError(rc, msg.decode() if msg else "")

@@ -1,0 +1,608 @@
+// Batched sweep: many cavities of different size and parameters advanced by
+// one persistent kernel launch that runs every requested step, captured once
+// into a CUDA graph and replayed.  Each block walks a flat list of tiles
+// covering every cavity; a grid-wide barrier separates the steps (each step
+// reads the whole previous lattice of its cavity).  The per-node work is the
+// same device code as the single-cavity step kernel, so a cavity advanced
+// here matches the same cavity advanced alone bit for bit.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace lbm {
+
+template <class R> struct CavDesc {
+    Geom gm;
+    void* buf[2];  // B_n / B_{n+1} ping-pong of this cavity
+    Coef<R> c;
+};
+
+struct Tile {
+    int cav, x0, y0;
+};
+
+// Bounded sense-reversing grid barrier.  Thread 0 of each block arrives on
+// count; the last arrival resets count and bumps gen; the others wait for gen
+// to change, at most `limit` polls of ~0.1-1 us each.  Returns false (in every
+// thread of the block) when the wait ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
+                                             long long limit, int* flag) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd((unsigned*)gen, 1u);
+        } else {
+            long long polls = 0;
+            while (*gen == g) {
+                if (++polls > limit) {
+                    ok = 0;
+                    atomicOr(flag, 1);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// One launch runs `nsteps` steps of every cavity.  Buffer parity `par` of
+// every cavity holds B_n on entry.
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 2) k_batch(const CavDesc<typename T::R>* __restrict__ cavs,
+                                               const Tile* __restrict__ tiles, int ntiles, int tw, int th,
+                                               long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
+                                               long long wait_limit, int* __restrict__ status,
+                                               int* __restrict__ timeout_flag) {
+    using R = typename T::R;
+    __shared__ CavDesc<R> cd;
+    __shared__ int cur_cav;
+    if (threadIdx.x == 0) cur_cav = -1;
+    for (long s = 0; s < nsteps; ++s) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const Tile tl = tiles[t];
+            __syncthreads();
+            if (tl.cav != cur_cav) {
+                // stage this cavity's descriptor in shared memory
+                const int* srcw = (const int*)&cavs[tl.cav];
+                int* dstw = (int*)&cd;
+                for (int k = threadIdx.x; k < (int)(sizeof(CavDesc<R>) / sizeof(int)); k += blockDim.x)
+                    dstw[k] = srcw[k];
+                __syncthreads();
+                if (threadIdx.x == 0) cur_cav = tl.cav;
+            }
+            __syncthreads();
+            const Geom gm = cd.gm;
+            const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
+            const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
+            for (int k = threadIdx.x; k < tw * th; k += blockDim.x) {
+                const int x = tl.x0 + k % tw, y = tl.y0 + k / tw;
+                if (x >= gm.nx || y >= gm.ny) continue;
+                R d[9], h[5];
+                Drag<R> dr;
+                const Macro<R> mc = node_state<T, false>(cd.c, gm, src, nullptr, x, y, dr, d, h);
+                if (!(mc.umag < R(0.5))) atomicOr(&status[tl.cav], 1);
+                collide<R>(cd.c, dr.iphi, mc, d, h);
+                const int off = y * gm.pitch + x;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+            }
+        }
+        par ^= 1;
+        if (s + 1 < nsteps) {
+            __threadfence();
+            if (!grid_barrier(bar_count, bar_gen, gridDim.x, wait_limit, timeout_flag)) return;
+        }
+    }
+}
+
+// Mean Nusselt numbers (Eq. 38) of every cavity, one block per cavity, FP64.
+template <class T>
+__global__ void __launch_bounds__(256) k_batch_nusselt(const CavDesc<typename T::R>* __restrict__ cavs,
+                                                       int prev_par, const double* __restrict__ Ls,
+                                                       double* __restrict__ out) {
+    using R = typename T::R;
+    __shared__ double sh[2][32];
+    const CavDesc<R>& cd = cavs[blockIdx.x];
+    const Geom gm = cd.gm;
+    const Src<T> prev = src_view<T>(cd.buf[prev_par], gm.plane);
+    const double L = Ls[2 * blockIdx.x], dT = Ls[2 * blockIdx.x + 1];
+    double wl = 0.0, wr = 0.0;
+    for (int y = threadIdx.x; y < gm.ny; y += blockDim.x) {
+        double tl[5], tr[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            tl[k] = (double)node_dT<T>(cd.c, gm, prev, k, y);
+            tr[k] = (double)node_dT<T>(cd.c, gm, prev, gm.nx - 1 - k, y);
+        }
+        const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
+        const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
+        const double wt = (y == 0 || y == gm.ny - 1) ? 0.5 : 1.0;
+        wl += wt * (-L * dl / dT);
+        wr += wt * (-L * dr / dT);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wl += __shfl_xor_sync(0xffffffffu, wl, o);
+        wr += __shfl_xor_sync(0xffffffffu, wr, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = wl;
+        sh[1][warp] = wr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        out[2 * blockIdx.x] = a / (double)(gm.ny - 1);
+        out[2 * blockIdx.x + 1] = b / (double)(gm.ny - 1);
+    }
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------------
+
+namespace {
+
+constexpr long long kDefaultWaitPolls = 20000000;  // ~2-20 s of 100 ns polls
+
+struct TuneChoice {
+    int tw = 128, th = 2, blocks_per_sm = 0;
+};
+
+}  // namespace
+
+struct lbm_batch_s {
+    int ncav = 0;
+    int precision = LBM_F32;
+    std::vector<lbm_params> params;
+    std::vector<Derived> dv;
+    std::vector<Geom> gm;
+    std::vector<CoefSet> coef;
+    std::vector<size_t> off[2];
+    size_t pool_bytes = 0;
+    void* pool = nullptr;
+    void* descs = nullptr;  // CavDesc<R>[ncav]
+    Tile* tiles = nullptr;
+    int ntiles = 0;
+    double* Ls = nullptr;   // (L, dT) per cavity
+    double* nu_dev = nullptr;
+    int* status = nullptr;  // per cavity
+    int* timeout_flag = nullptr;
+    unsigned* bar = nullptr;  // count, gen
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int par = 0;  // parity holding B_n
+    long t = 0;
+    TuneChoice tune;
+    int nblocks = 0;
+    long long wait_limit = kDefaultWaitPolls;
+    cudaGraphExec_t gexec = nullptr;
+    long gexec_steps = 0;
+    int gexec_par = -1;
+    long long gexec_limit = -1;
+    std::string err;
+    std::string signature;
+};
+
+namespace {
+
+int bfail(lbm_batch b, int code, const std::string& m) {
+    if (b) b->err = m;
+    else set_global_error(m);
+    return code;
+}
+
+#define BCK(b, expr)                                                                     \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T> const void* kernel_ptr() { return (const void*)&k_batch<T>; }
+
+int build_tiles(lbm_batch b) {
+    std::vector<Tile> tl;
+    for (int c = 0; c < b->ncav; ++c)
+        for (int y0 = 0; y0 < b->gm[c].ny; y0 += b->tune.th)
+            for (int x0 = 0; x0 < b->gm[c].nx; x0 += b->tune.tw) tl.push_back(Tile{c, x0, y0});
+    if (b->tiles) cudaFree(b->tiles);
+    b->tiles = nullptr;
+    b->ntiles = (int)tl.size();
+    BCK(b, cudaMalloc(&b->tiles, sizeof(Tile) * tl.size()));
+    BCK(b, cudaMemcpy(b->tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+int grid_size(lbm_batch b, int* nblocks) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    BCK(b, cudaGetDevice(&dev));
+    BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>() : kernel_ptr<PrecF32P>();
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
+    if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "batched kernel cannot be resident");
+    int want = b->tune.blocks_per_sm > 0 ? std::min(b->tune.blocks_per_sm, per_sm) : per_sm;
+    *nblocks = std::max(1, std::min(nsm * want, b->ntiles));
+    return LBM_OK;
+}
+
+int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
+    void* args[13];
+    long ns = nsteps;
+    int pr = par;
+    unsigned* cnt = b->bar;
+    unsigned* gen = b->bar + 1;
+    long long lim = b->wait_limit;
+    int tw = b->tune.tw, th = b->tune.th, nt = b->ntiles;
+    const void* descs = b->descs;
+    const Tile* tiles = b->tiles;
+    args[0] = &descs;
+    args[1] = &tiles;
+    args[2] = &nt;
+    args[3] = &tw;
+    args[4] = &th;
+    args[5] = &ns;
+    args[6] = &pr;
+    args[7] = &cnt;
+    args[8] = &gen;
+    args[9] = &lim;
+    args[10] = &b->status;
+    args[11] = &b->timeout_flag;
+    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>() : kernel_ptr<PrecF32P>();
+    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+template <class R> int upload_descs(lbm_batch b) {
+    std::vector<CavDesc<R>> h(b->ncav);
+    for (int c = 0; c < b->ncav; ++c) {
+        h[c].gm = b->gm[c];
+        h[c].buf[0] = (char*)b->pool + b->off[0][c];
+        h[c].buf[1] = (char*)b->pool + b->off[1][c];
+        if constexpr (sizeof(R) == 8) h[c].c = b->coef[c].d;
+        else h[c].c = b->coef[c].f;
+    }
+    if (!b->descs) BCK(b, cudaMalloc(&b->descs, sizeof(CavDesc<R>) * b->ncav));
+    BCK(b, cudaMemcpy(b->descs, h.data(), sizeof(CavDesc<R>) * b->ncav, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+// Rest state in both buffers of every cavity, then one step (S_0 -> B_0).
+int reset(lbm_batch b) {
+    BCK(b, cudaMemsetAsync(b->pool, 0, b->pool_bytes, b->stream));
+    BCK(b, cudaMemsetAsync(b->status, 0, sizeof(int) * b->ncav, b->stream));
+    BCK(b, cudaMemsetAsync(b->timeout_flag, 0, sizeof(int), b->stream));
+    BCK(b, cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream));
+    int rc = launch(b, 1, 0, b->stream);
+    if (rc != LBM_OK) return rc;
+    b->par = 1;
+    b->t = 0;
+    return LBM_OK;
+}
+
+void drop_graph(lbm_batch b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gexec_steps = 0;
+    b->gexec_par = -1;
+}
+
+int run_steps(lbm_batch b, long nsteps, cudaStream_t s) {
+    if (nsteps <= 0) return LBM_OK;
+    const int par = b->par;
+    if (!(b->gexec && b->gexec_steps == nsteps && b->gexec_par == par && b->gexec_limit == b->wait_limit)) {
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = launch(b, nsteps, par, b->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+        if (rc != LBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+        cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->gexec_steps = nsteps;
+        b->gexec_par = par;
+        b->gexec_limit = b->wait_limit;
+    }
+    BCK(b, cudaGraphLaunch(b->gexec, s));
+    if (nsteps & 1) b->par ^= 1;
+    return LBM_OK;
+}
+
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp pr;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    std::string n = pr.name;
+    std::replace(n.begin(), n.end(), ' ', '_');
+    return n;
+}
+
+// Autotuner cache: one line per (signature) -> "tw th blocks_per_sm".
+bool cache_lookup(const std::string& path, const std::string& sig, TuneChoice* tc) {
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ss(line);
+        std::string key;
+        TuneChoice t;
+        if (ss >> key >> t.tw >> t.th >> t.blocks_per_sm && key == sig) {
+            *tc = t;
+            return true;
+        }
+    }
+    return false;
+}
+
+void cache_store(const std::string& path, const std::string& sig, const TuneChoice& tc) {
+    std::ofstream out(path, std::ios::app);
+    if (out) out << sig << " " << tc.tw << " " << tc.th << " " << tc.blocks_per_sm << "\n";
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || ncav <= 0) return bfail(nullptr, LBM_ERR_ARG, "need at least one cavity");
+    const int prec = p[0].precision;
+    if (prec != LBM_F32 && prec != LBM_F64) return bfail(nullptr, LBM_ERR_ARG, "batched cavities run in FP32 or FP64");
+    lbm_batch b = new lbm_batch_s();
+    b->ncav = ncav;
+    b->precision = prec;
+    b->params.assign(p, p + ncav);
+    b->dv.resize(ncav);
+    b->gm.resize(ncav);
+    b->coef.resize(ncav);
+    b->off[0].resize(ncav);
+    b->off[1].resize(ncav);
+    b->stream = (cudaStream_t)stream;
+    std::ostringstream sig;
+    sig << device_name() << ":p" << prec << ":n" << ncav;
+    unsigned long long hsh = 1469598103934665603ull;
+    size_t at = 0;
+    for (int c = 0; c < ncav; ++c) {
+        std::string why;
+        if (p[c].precision != prec) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_ARG, "every cavity of a batch needs the same precision");
+        }
+        if (p[c].use_phi_field) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_ARG, "batched cavities use uniform porosity");
+        }
+        int rc = setup_lattice(&p[c], &b->dv[c], &b->coef[c], &b->gm[c], &why);
+        if (rc != LBM_OK) {
+            delete b;
+            return bfail(nullptr, rc, "cavity " + std::to_string(c) + ": " + why);
+        }
+        const size_t bb = (state_buffer_bytes(prec, b->gm[c].plane) + 255) / 256 * 256;
+        b->off[0][c] = at;
+        b->off[1][c] = at + bb;
+        at += 2 * bb;
+        hsh = (hsh ^ (unsigned long long)(p[c].nx * 65537 + p[c].ny)) * 1099511628211ull;
+    }
+    sig << ":h" << std::hex << hsh;
+    b->signature = sig.str();
+    b->pool_bytes = at;
+    cudaError_t e = cudaSuccess;
+#define BI(expr)                                                    \
+    do {                                                            \
+        e = (expr);                                                 \
+        if (e != cudaSuccess) {                                     \
+            std::string m_ = std::string(#expr) + ": " + cudaGetErrorString(e); \
+            lbm_batch_destroy(b);                                   \
+            return bfail(nullptr, LBM_ERR_CUDA, m_);                \
+        }                                                           \
+    } while (0)
+    BI(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    BI(cudaMalloc(&b->pool, b->pool_bytes));
+    BI(cudaMalloc(&b->status, sizeof(int) * ncav));
+    BI(cudaMalloc(&b->timeout_flag, sizeof(int)));
+    BI(cudaMalloc(&b->bar, 2 * sizeof(unsigned)));
+    BI(cudaMalloc(&b->Ls, sizeof(double) * 2 * ncav));
+    BI(cudaMalloc(&b->nu_dev, sizeof(double) * 2 * ncav));
+#undef BI
+    std::vector<double> Ls(2 * ncav);
+    for (int c = 0; c < ncav; ++c) {
+        Ls[2 * c] = b->dv[c].L;
+        Ls[2 * c + 1] = b->dv[c].dT;
+    }
+    int rc = LBM_OK;
+    if (cudaMemcpy(b->Ls, Ls.data(), sizeof(double) * 2 * ncav, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = bfail(b, LBM_ERR_CUDA, "parameter upload");
+    if (rc == LBM_OK) rc = prec == LBM_F64 ? upload_descs<double>(b) : upload_descs<float>(b);
+    if (rc == LBM_OK) rc = build_tiles(b);
+    if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
+    if (rc == LBM_OK) rc = reset(b);
+    if (rc != LBM_OK) {
+        std::string m = b->err;
+        lbm_batch_destroy(b);
+        return bfail(nullptr, rc, m);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, long nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
+    int rc = run_steps(b, nsteps, b->stream);
+    if (rc == LBM_OK) b->t += nsteps;
+    return rc;
+}
+
+int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    const int prev = b->par ^ 1;
+    if (b->precision == LBM_F64)
+        k_batch_nusselt<PrecF64P><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<double>*)b->descs, prev, b->Ls,
+                                                                 b->nu_dev);
+    else
+        k_batch_nusselt<PrecF32P><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
+                                                                 b->nu_dev);
+    BCK(b, cudaGetLastError());
+    std::vector<double> h(2 * b->ncav);
+    BCK(b, cudaMemcpyAsync(h.data(), b->nu_dev, sizeof(double) * 2 * b->ncav, cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int c = 0; c < b->ncav; ++c) {
+        if (nu_hot) nu_hot[c] = h[2 * c];
+        if (nu_cold) nu_cold[c] = h[2 * c + 1];
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_status(lbm_batch b, int* status) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    std::vector<int> h(b->ncav);
+    int to = 0;
+    BCK(b, cudaMemcpyAsync(h.data(), b->status, sizeof(int) * b->ncav, cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaMemcpyAsync(&to, b->timeout_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    int any = 0;
+    for (int c = 0; c < b->ncav; ++c) {
+        if (status) status[c] = h[c] ? LBM_ERR_DIVERGED : LBM_OK;
+        any |= h[c];
+    }
+    if (to) return bfail(b, LBM_ERR_TIMEOUT, "a grid-barrier wait ran out; the lattice state is incomplete");
+    if (any) return bfail(b, LBM_ERR_DIVERGED, "at least one cavity raised its divergence flag");
+    return LBM_OK;
+}
+
+int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (cav < 0 || cav >= b->ncav || !f_dev || !g_dev) return bfail(b, LBM_ERR_ARG, "bad cavity or output");
+    ReadStateLaunch L;
+    L.precision = b->precision;
+    L.prev = (char*)b->pool + b->off[b->par ^ 1][cav];
+    L.phi = nullptr;
+    L.gm = b->gm[cav];
+    L.f = f_dev;
+    L.g = g_dev;
+    L.nblocks = kReduceBlocks;
+    L.stream = b->stream;
+    BCK(b, launch_read_state(L, b->coef[cav]));
+    return LBM_OK;
+}
+
+int lbm_batch_set_wait_limit(lbm_batch b, long long polls) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (polls < 0) return bfail(b, LBM_ERR_ARG, "polls < 0");
+    b->wait_limit = polls;
+    BCK(b, cudaMemsetAsync(b->timeout_flag, 0, sizeof(int), b->stream));
+    BCK(b, cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    TuneChoice best;
+    bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);
+    if (!cached) {
+        const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1}};
+        const int occ[] = {0, 4, 2};
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        BCK(b, cudaEventCreate(&e0));
+        BCK(b, cudaEventCreate(&e1));
+        const long nsteps = 20;
+        for (auto& sh : shapes)
+            for (int o : occ) {
+                b->tune.tw = sh[0];
+                b->tune.th = sh[1];
+                b->tune.blocks_per_sm = o;
+                int rc = build_tiles(b);
+                if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
+                drop_graph(b);
+                if (rc == LBM_OK) rc = run_steps(b, 2, b->stream);  // warm
+                if (rc != LBM_OK) return rc;
+                BCK(b, cudaEventRecord(e0, b->stream));
+                rc = run_steps(b, nsteps, b->stream);
+                if (rc != LBM_OK) return rc;
+                BCK(b, cudaEventRecord(e1, b->stream));
+                BCK(b, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = b->tune;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cache_path) cache_store(cache_path, b->signature, best);
+    }
+    b->tune = best;
+    int rc = build_tiles(b);
+    if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
+    drop_graph(b);
+    if (rc == LBM_OK) rc = reset(b);  // tuning advanced the lattices: start again from t = 0
+    if (rc != LBM_OK) return rc;
+    if (tile_w) *tile_w = best.tw;
+    if (tile_h) *tile_h = best.th;
+    if (blocks_per_sm) *blocks_per_sm = best.blocks_per_sm;
+    return LBM_OK;
+}
+
+int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (t) *t = b->t;
+    if (ntiles) *ntiles = b->ntiles;
+    if (nblocks) *nblocks = b->nblocks;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b) {
+    if (!b) return LBM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->pool) cudaFree(b->pool);
+    if (b->descs) cudaFree(b->descs);
+    if (b->tiles) cudaFree(b->tiles);
+    if (b->Ls) cudaFree(b->Ls);
+    if (b->nu_dev) cudaFree(b->nu_dev);
+    if (b->status) cudaFree(b->status);
+    if (b->timeout_flag) cudaFree(b->timeout_flag);
+    if (b->bar) cudaFree(b->bar);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(lbm_batch b) { return b ? b->err.c_str() : lbm_last_error(nullptr); }
+
+}  // extern "C"

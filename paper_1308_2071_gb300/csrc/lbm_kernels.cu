@@ -26,9 +26,9 @@ __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const type
     collide<R>(c, dr.iphi, mc, d, h);
     const int off = y * gm.pitch + x;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R>::st(dst.f + i * gm.plane + off, d[i]);
+    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R>::st(dst.g + j * gm.plane + off, h[j]);
+    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
 }
 
 // ---- observables ------------------------------------------------------------------
@@ -107,23 +107,6 @@ __global__ void __launch_bounds__(256) k_observe(Src<T> prev, const typename T::
 #pragma unroll
         for (int k = 0; k < 4; ++k) partials[blockIdx.x * 4 + k] = v[k];
     }
-}
-
-// T - T0 of the post-stream state at node (x, y), pulled from B_{n-1}.
-template <class T>
-__device__ __forceinline__ typename T::R node_dT(const Coef<typename T::R>& c, const Geom& gm,
-                                                 const Src<T>& prev, int x, int y) {
-    using R = typename T::R;
-    const Normal nr = normal_of(gm, x, y);
-    if (nr.dx == 0 && nr.dy == 0) return pull_heat<T>(prev, gm, y * gm.pitch + x) + c.qhalf;
-    if (gm.thermal_bc == 1) return c.dTc;
-    if (nr.dx != 0) return x == 0 ? c.dTh : c.dTc;
-    const R dTf = pull_heat<T>(prev, gm, (y + nr.dy) * gm.pitch + x) + c.qhalf;
-    if (gm.adi_order == 2) {
-        const R dTff = pull_heat<T>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x) + c.qhalf;
-        return (R(4) * dTf - dTff) * R(1.0 / 3.0);
-    }
-    return dTf;
 }
 
 // One block: folds the per-block partials in a fixed order and evaluates the

@@ -149,3 +149,87 @@ class Cavity:
         cur = torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
+
+
+class Batch:
+    """Many independent cavities advanced by one persistent launch per call.
+
+    cavities: list of dicts with nx, ny, Ra, Da, phi and optional Section 4
+    overrides (Pr, J, Ma, ...); all share one precision ("f32" or "f64")."""
+
+    def __init__(self, cavities, precision: str = "f32", stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device")
+        lib = L.load()
+        n = len(cavities)
+        arr = (L.Params * n)()
+        for k, cv in enumerate(cavities):
+            cv = dict(cv)
+            p = make_params(cv.pop("nx"), cv.pop("ny"), cv.pop("Ra"), cv.pop("Da"), cv.pop("phi"), precision,
+                            **cv)
+            arr[k] = p
+        self.params = arr
+        self.ncav = n
+        self.sizes = [(c["nx"], c["ny"]) for c in cavities]
+        self.stream = stream or torch.cuda.current_stream()
+        self.device = self.stream.device
+        self._b = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lbm_batch_init(arr, n, C.c_void_p(self.stream.cuda_stream), C.byref(self._b))
+        L.check(rc, None)
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            L.load().lbm_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        L.check(rc, batch=self._b)
+
+    def step(self, n: int = 1) -> "Batch":
+        self._check(L.load().lbm_batch_step(self._b, int(n)))
+        return self
+
+    def nusselt(self):
+        import numpy as np
+
+        hot = np.zeros(self.ncav)
+        cold = np.zeros(self.ncav)
+        self._check(L.load().lbm_batch_nusselt(self._b, hot.ctypes.data, cold.ctypes.data))
+        return hot, cold
+
+    def status(self):
+        """(return code, per-cavity status array)."""
+        import numpy as np
+
+        st = np.zeros(self.ncav, dtype=np.int32)
+        rc = L.load().lbm_batch_status(self._b, st.ctypes.data)
+        return rc, st
+
+    def read_state(self, cav: int):
+        nx, ny = self.sizes[cav]
+        f = torch.empty((9, ny, nx), dtype=torch.float64, device=self.device)
+        g = torch.empty((5, ny, nx), dtype=torch.float64, device=self.device)
+        self._check(L.load().lbm_batch_read_state(self._b, cav, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr())))
+        self.stream.synchronize()
+        return f, g
+
+    def set_wait_limit(self, polls: int):
+        self._check(L.load().lbm_batch_set_wait_limit(self._b, int(polls)))
+
+    def tune(self, cache_path: str | None = None):
+        tw, th, bps = C.c_int(), C.c_int(), C.c_int()
+        path = cache_path.encode() if cache_path else None
+        self._check(L.load().lbm_batch_tune(self._b, path, C.byref(tw), C.byref(th), C.byref(bps)))
+        return tw.value, th.value, bps.value
+
+    def query(self):
+        t, nt, nb = C.c_long(), C.c_int(), C.c_int()
+        self._check(L.load().lbm_batch_query(self._b, C.byref(t), C.byref(nt), C.byref(nb)))
+        return dict(t=t.value, ntiles=nt.value, nblocks=nb.value)
