@@ -245,6 +245,30 @@ def batched_leg(steps, warmup, ncav=256, seed=2071):
                 status=int(rc), sizes="U{64..512} square, seed %d" % seed)
 
 
+def adjoint_leg(n=512, nsteps=2000, ckpt=100):
+    """Gradient of the hot-wall mean Nusselt number after nsteps with respect to
+    a per-cell porosity field (phi_bar 0.6 plus a seeded perturbation), FP32,
+    checkpoint every ckpt steps; adjoint MLUPS = node-steps of the forward
+    sweep / wall time of the whole gradient (forward, recompute, reverse)."""
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    phi = torch.from_numpy(perturbed_porosity(n, n, phi_bar=0.6, amplitude=0.05, corr_len=8.0, seed=2000))
+    cav = Cavity(n, n, Ra=1e5, Da=1e-2, phi=0.6, precision="f32", phi_field=phi.cuda())
+    cav.adjoint(50, 10)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g = cav.adjoint(nsteps, ckpt)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    cav.close()
+    return dict(workload=f"{n}x{n}, Ra 1e5, Da 1e-2, {nsteps} steps, checkpoint every {ckpt}, FP32",
+                mlups=round(n * n * nsteps / dt / 1e6, 2), seconds=round(dt, 3), J=J,
+                grad_l2=float(g.double().norm()))
+
+
 def cpu_leg(n, seconds, warmup=1, max_steps=None):
     """The FP64 oracle as it stands, on every host core, on a bounded number of
     steps of the same lattice; returns (MLUPS, threads, steps, seconds)."""
@@ -329,6 +353,7 @@ def main():
         line["variants"] = variants
         line["e2e"] = e2e_leg(a.size, a.precision, min(a.steps, 1000))
         line["batched"] = batched_leg(min(a.steps, 1000), 8)
+        line["adjoint"] = adjoint_leg()
         mlc, threads, k, dt = cpu_leg(a.size, a.cpu_seconds)
         line["cpu_baseline"] = dict(value=round(mlc, 3), unit="MLUPS", cores=threads, kind="oracle",
                                     sample=f"{k} steps of the {a.size}^2 lattice, FP64 oracle, {dt:.1f} s")

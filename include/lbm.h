@@ -126,6 +126,20 @@ int lbm_step(lbm_handle h, long nsteps);
 int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev,
                     void* p_dev);
 
+/* Discrete adjoint (no counterpart in the paper, which has no gradient).
+ * Resets the handle to its initial state, runs nsteps steps forward keeping
+ * one lattice every ckpt_every steps, evaluates J = mean Nu of the hot wall
+ * (Eq. 38) at t = nsteps, then sweeps backwards, recomputing each segment of
+ * ckpt_every states from its checkpoint, and writes dJ/dphi for every cell
+ * (ny*nx dense device values, double for LBM_F64, float for LBM_F32) to
+ * dJdphi_dev; *J (host, may be NULL) receives J.  The porosity enters through
+ * the per-cell Ergun drag (Eq. 4-5) and the equilibria (Eq. 14, 16, 19, 23).
+ * The handle ends at t = nsteps.  Needs use_phi_field = 1, LBM_F64 or LBM_F32,
+ * first-order adiabatic walls.  Allocates (nsteps/ckpt_every + ckpt_every + 2)
+ * lattices of temporary device memory for the call.  Synchronises.
+ * Errors: LBM_ERR_STATE (no porosity field), LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void* dJdphi_dev);
+
 /* Mean Nusselt numbers (Eq. 38) of the walls x = 0 and x = nx - 1 of the
  * current state, FP64; reads only the five node columns next to each wall.
  * Synchronises the stream. */

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("lbm_set_porous_field", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lbm_step", C.c_int, [C.c_void_p, C.c_long]),
     ("lbm_observables", C.c_int, [C.c_void_p, C.POINTER(Obs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lbm_adjoint_step", C.c_int, [C.c_void_p, C.c_long, C.c_long, C.POINTER(C.c_double), C.c_void_p]),
     ("lbm_nusselt", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lbm_read_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_checkpoint_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),

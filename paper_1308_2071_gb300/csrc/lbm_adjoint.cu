@@ -1,0 +1,199 @@
+// Discrete adjoint of the time stepping: gradient of the mean Nusselt number
+// of the hot wall (Eq. 38) after N steps with respect to a per-cell porosity
+// field, by reverse sweeps with checkpoint-and-recompute.
+//
+// Notation: B_k is the post-collision lattice after step k (B_{-1} = rest),
+// S_N = pull(B_{N-1}) + wall rule, J = Nu_hot(S_N).  The adjoint state
+// M^(k)(x) = dJ / d(populations pulled into node x at step k) lives on nodes;
+// dJ/dB_k(y)_i = M^(k)_i(y + e_i) is gathered (the reverse of the pull, read
+// over reversed directions, so no atomics).  A wall node uses the pulled
+// populations of its inner neighbour, so a fluid node also folds in the
+// reverse of the wall nodes that extrapolate from it.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "lbm_adjoint.cuh"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace lbm {
+
+// dJ/dS_N as the initial adjoint state: J depends on T at the columns 1..4
+// next to the hot wall (the wall column is the imposed T_h); on first-order
+// adiabatic walls T(x, 0) = T(x, 1) and T(x, ny-1) = T(x, ny-2).
+template <class R>
+__global__ void k_adj_seed(R* __restrict__ M, Geom gm, double L, double dT) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y < 1 || y > gm.ny - 2) return;
+    const double cx[5] = {-25.0, 48.0, -36.0, 16.0, -3.0};
+    double wy = 1.0;
+    if (gm.thermal_bc == 0) {
+        if (y == 1) wy += 0.5;
+        if (y == gm.ny - 2) wy += 0.5;
+    }
+    for (int x = 1; x <= 4 && x <= gm.nx - 2; ++x) {
+        const double a = -L * cx[x] / (12.0 * dT * (double)(gm.ny - 1)) * wy;
+        for (int j = 0; j < 5; ++j) M[(9 + j) * gm.plane + y * gm.pitch + x] = (R)a;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void gather_adjoint(const R* __restrict__ M, const Geom& gm, int x, int y, R (&lf)[9],
+                                               R (&lh)[5]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int xs = x + ex9(i), ys = y + ey9(i);
+        const bool in = xs >= 0 && xs < gm.nx && ys >= 0 && ys < gm.ny;
+        lf[i] = in ? M[i * gm.plane + ys * gm.pitch + xs] : R(0);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int xs = x + ex9(j), ys = y + ey9(j);
+        const bool in = xs >= 0 && xs < gm.nx && ys >= 0 && ys < gm.ny;
+        lh[j] = in ? M[(9 + j) * gm.plane + ys * gm.pitch + xs] : R(0);
+    }
+}
+
+__device__ __forceinline__ bool wall_is_dirichlet(const Geom& gm, Normal nr) {
+    return gm.thermal_bc == 1 || nr.dx != 0;
+}
+
+template <class R>
+__device__ __forceinline__ R wall_dT(const Coef<R>& c, const Geom& gm, int x) {
+    return gm.thermal_bc == 1 ? c.dTc : (x == 0 ? c.dTh : c.dTc);
+}
+
+// One reverse step: from M^(k+1) and the forward input B_k to M^(k), adding
+// this step's porosity sensitivities to gphi.
+template <class T>
+__global__ void __launch_bounds__(256) k_adjoint(Src<T> state, const typename T::R* __restrict__ Mnext,
+                                                 typename T::R* __restrict__ Mcur,
+                                                 const typename T::P* __restrict__ phi, double* __restrict__ gphi,
+                                                 Geom gm, Coef<typename T::R> c) {
+    using R = typename T::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= gm.nx || y >= gm.ny) return;
+    const int off = y * gm.pitch + x;
+    const long k = (long)y * gm.nx + x;
+    const Normal nr = normal_of(gm, x, y);
+    R lf[9], lh[5];
+    if (nr.dx != 0 || nr.dy != 0) {
+        // wall node: it reads no pulled populations of its own; its porosity
+        // sensitivity is computed here, its inner neighbour's by that node
+#pragma unroll
+        for (int q = 0; q < NPOP; ++q) Mcur[q * gm.plane + off] = R(0);
+        gather_adjoint<R>(Mnext, gm, x, y, lf, lh);
+        const int xf = x + nr.dx, yf = y + nr.dy, offf = yf * gm.pitch + xf;
+        R df[9], hf[5];
+        pull<T>(state, gm, offf, df, hf);
+        Tape<R> tf;
+        tape_node<R>(c, (R)phi[offf], df, hf, tf);
+        R dfb[9] = {R(0)}, hfb[5] = {R(0)}, pfb = R(0);
+        const R pb = wall_node_adjoint<R>(c, tf, (R)phi[off], wall_is_dirichlet(gm, nr), wall_dT<R>(c, gm, x), lf, lh,
+                                          dfb, hfb, pfb);
+        gphi[k] += (double)pb;
+        return;
+    }
+    gather_adjoint<R>(Mnext, gm, x, y, lf, lh);
+    R d[9], h[5];
+    pull<T>(state, gm, off, d, h);
+    Tape<R> t;
+    tape_node<R>(c, (R)phi[off], d, h, t);
+    R db[9] = {R(0)}, hb[5] = {R(0)}, pb = R(0);
+    fluid_node_adjoint<R>(c, t, lf, lh, db, hb, pb);
+    // wall nodes b = x - n whose inward normal n points at this node
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            const int xb = x - dx, yb = y - dy;
+            const Normal nb = normal_of(gm, xb, yb);
+            if (nb.dx != dx || nb.dy != dy) continue;
+            R lfb[9], lhb[5];
+            gather_adjoint<R>(Mnext, gm, xb, yb, lfb, lhb);
+            (void)wall_node_adjoint<R>(c, t, (R)phi[yb * gm.pitch + xb], wall_is_dirichlet(gm, nb),
+                                       wall_dT<R>(c, gm, xb), lfb, lhb, db, hb, pb);
+        }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Mcur[i * gm.plane + off] = db[i];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Mcur[(9 + j) * gm.plane + off] = hb[j];
+    gphi[k] += (double)pb;
+}
+
+template <class Out>
+__global__ void k_adj_out(const double* __restrict__ g, Out* __restrict__ out, long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        out[k] = (Out)g[k];
+}
+
+}  // namespace lbm
+
+namespace {
+
+template <class T>
+cudaError_t adjoint_sweep(const AdjointJob& J) {
+    using R = typename T::R;
+    const Geom& gm = J.gm;
+    const Coef<R>& c = *(const Coef<R>*)J.coef;
+    const int N = (int)J.nsteps, K = (int)J.ckpt_every;
+    const size_t buf = J.buf_bytes;
+    const size_t mbytes = (size_t)gm.plane * NPOP * sizeof(R);
+    cudaStream_t s = J.stream;
+    dim3 blk(128, 2), grd((gm.nx + 127) / 128, (gm.ny + 1) / 2);
+    const int nseg = (N + K - 1) / K;
+    R* M[2] = {(R*)J.madj, (R*)J.madj + (size_t)gm.plane * NPOP};
+    cudaError_t e = cudaMemsetAsync(M[0], 0, mbytes, s);
+    if (e != cudaSuccess) return e;
+    k_adj_seed<R><<<(gm.ny + 255) / 256, 256, 0, s>>>(M[0], gm, J.L, J.dT);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(J.gphi, 0, sizeof(double) * (size_t)gm.nx * gm.ny, s)) != cudaSuccess) return e;
+    int a = 0;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int j0 = sg * K, len = (N - j0) < K ? (N - j0) : K;
+        // slot 0 is the checkpoint; recompute slots 1..len-1 with the forward step
+        std::vector<const void*> slot(len);
+        slot[0] = (const char*)J.ckpt + (size_t)sg * buf;
+        for (int m = 1; m < len; ++m) {
+            void* dst = (char*)J.seg + (size_t)(m - 1) * buf;
+            StepLaunch L;
+            L.precision = J.precision;
+            L.src = slot[m - 1];
+            L.dst = dst;
+            L.phi = J.phi;
+            L.gm = gm;
+            L.bx = 128;
+            L.by = 2;
+            L.status = J.status;
+            L.stream = s;
+            CoefSet cs;
+            if (sizeof(R) == 8) cs.d = *(const Coef<double>*)J.coef;
+            else cs.f = *(const Coef<float>*)J.coef;
+            if ((e = launch_step(L, cs)) != cudaSuccess) return e;
+            slot[m] = dst;
+        }
+        for (int j = j0 + len - 1; j >= j0; --j) {
+            const Src<T> st = src_view<T>(slot[j - j0], gm.plane);
+            k_adjoint<T><<<grd, blk, 0, s>>>(st, M[a], M[a ^ 1], (const typename T::P*)J.phi, J.gphi, gm, c);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            a ^= 1;
+        }
+    }
+    const long n = (long)gm.nx * gm.ny;
+    if (sizeof(R) == 8) k_adj_out<double><<<kReduceBlocks, 256, 0, s>>>(J.gphi, (double*)J.out, n);
+    else k_adj_out<float><<<kReduceBlocks, 256, 0, s>>>(J.gphi, (float*)J.out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace lbm {
+cudaError_t launch_adjoint_sweep(const AdjointJob& J) {
+    if (J.precision == PREC_F64) return adjoint_sweep<PrecF64>(J);
+    return adjoint_sweep<PrecF32>(J);
+}
+}  // namespace lbm

@@ -447,6 +447,77 @@ int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
     return LBM_OK;
 }
 
+int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void* dJdphi_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "the adjoint needs a handle created with use_phi_field = 1");
+    if (h->precision == LBM_F32_STORE_F16) return fail(h, LBM_ERR_ARG, "the adjoint runs in LBM_F64 or LBM_F32");
+    if (h->p.adiabatic_order != 1) return fail(h, LBM_ERR_ARG, "the adjoint supports first-order adiabatic walls");
+    if (nsteps < 1 || ckpt_every < 1 || !dJdphi_dev) return fail(h, LBM_ERR_ARG, "need nsteps >= 1, ckpt_every >= 1, output");
+    const long N = nsteps, K = ckpt_every < nsteps ? ckpt_every : nsteps;
+    const long nseg = (N + K - 1) / K;
+    const size_t rsz = h->precision == LBM_F64 ? sizeof(double) : sizeof(float);
+    void *ckpt = nullptr, *seg = nullptr, *madj = nullptr;
+    double* gphi = nullptr;
+    auto release = [&]() {
+        if (ckpt) cudaFree(ckpt);
+        if (seg) cudaFree(seg);
+        if (madj) cudaFree(madj);
+        if (gphi) cudaFree(gphi);
+    };
+    cudaError_t e = cudaMalloc(&ckpt, (size_t)nseg * h->buf_bytes);
+    if (e == cudaSuccess && K > 1) e = cudaMalloc(&seg, (size_t)(K - 1) * h->buf_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&madj, 2 * (size_t)h->gm.plane * NPOP * rsz);
+    if (e == cudaSuccess) e = cudaMalloc(&gphi, sizeof(double) * (size_t)h->p.nx * h->p.ny);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(h, e, "adjoint buffers");
+    }
+    // forward sweep from the initial state, keeping B_{sK-1} (state index j = sK)
+    int rc = reset_state(h);
+    if (rc == LBM_OK) {
+        e = cudaMemsetAsync(ckpt, 0, h->buf_bytes, h->stream);  // j = 0: the rest state B_{-1}
+        for (long t = 0; t < N && e == cudaSuccess; ++t) {
+            const long j = t + 1;  // buf[cur] holds B_t, state index j
+            if (j % K == 0 && j <= N - 1)
+                e = cudaMemcpyAsync((char*)ckpt + (size_t)(j / K) * h->buf_bytes, h->buf[h->cur], h->buf_bytes,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess) e = launch_step(step_launch(h, h->cur, h->stream), h->coef);
+            h->cur ^= 1;
+        }
+        h->t = N;
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint forward sweep");
+    }
+    if (rc == LBM_OK) {
+        double nuh = 0.0;
+        rc = lbm_nusselt(h, &nuh, nullptr);
+        if (rc == LBM_OK && J) *J = nuh;
+    }
+    if (rc == LBM_OK) {
+        AdjointJob A;
+        A.precision = h->precision;
+        A.gm = h->gm;
+        A.coef = h->precision == LBM_F64 ? (const void*)&h->coef.d : (const void*)&h->coef.f;
+        A.nsteps = N;
+        A.ckpt_every = K;
+        A.buf_bytes = h->buf_bytes;
+        A.ckpt = ckpt;
+        A.seg = seg;
+        A.madj = madj;
+        A.gphi = gphi;
+        A.phi = h->phi;
+        A.status = h->status_dev;
+        A.L = h->dv.L;
+        A.dT = h->dv.dT;
+        A.out = dJdphi_dev;
+        A.stream = h->stream;
+        e = launch_adjoint_sweep(A);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint reverse sweep");
+    }
+    release();
+    return rc;
+}
+
 int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!f_dev || !g_dev) return fail(h, LBM_ERR_ARG, "f_dev and g_dev are required");

@@ -76,22 +76,23 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 2) k_bat
                                                int* __restrict__ timeout_flag) {
     using R = typename T::R;
     __shared__ CavDesc<R> cd;
-    __shared__ int cur_cav;
-    if (threadIdx.x == 0) cur_cav = -1;
+    // each block owns a contiguous run of tiles (row-major within a cavity), so
+    // the cavity changes rarely and only then does the block synchronise
+    const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t0 = blockIdx.x * per, t1 = min(ntiles, t0 + per);
     for (long s = 0; s < nsteps; ++s) {
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int cur_cav = -1;
+        for (int t = t0; t < t1; ++t) {
             const Tile tl = tiles[t];
-            __syncthreads();
-            if (tl.cav != cur_cav) {
-                // stage this cavity's descriptor in shared memory
+            if (tl.cav != cur_cav) {  // block-uniform branch
+                __syncthreads();
                 const int* srcw = (const int*)&cavs[tl.cav];
                 int* dstw = (int*)&cd;
                 for (int k = threadIdx.x; k < (int)(sizeof(CavDesc<R>) / sizeof(int)); k += blockDim.x)
                     dstw[k] = srcw[k];
                 __syncthreads();
-                if (threadIdx.x == 0) cur_cav = tl.cav;
+                cur_cav = tl.cav;
             }
-            __syncthreads();
             const Geom gm = cd.gm;
             const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
             const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
@@ -229,6 +230,7 @@ int bfail(lbm_batch b, int code, const std::string& m) {
 template <class T> const void* kernel_ptr() { return (const void*)&k_batch<T>; }
 
 int build_tiles(lbm_batch b) {
+    if (b->stream) BCK(b, cudaStreamSynchronize(b->stream));  // queued launches may still read the old list
     std::vector<Tile> tl;
     for (int c = 0; c < b->ncav; ++c)
         for (int y0 = 0; y0 < b->gm[c].ny; y0 += b->tune.th)

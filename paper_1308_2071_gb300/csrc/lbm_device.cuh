@@ -250,7 +250,7 @@ __device__ __forceinline__ Macro<R> fluid_macros(const Coef<R>& c, const Drag<R>
 // Eq. 34 with n_eq of Eq. 29 and Psi of Eq. 30, then g+ = N^-1 n+ (Eq. 35,
 // N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h.
 template <class R>
-__device__ __forceinline__ void collide(const Coef<R>& c, R iphi, const Macro<R>& mc, R (&d)[9],
+__host__ __device__ __forceinline__ void collide(const Coef<R>& c, R iphi, const Macro<R>& mc, R (&d)[9],
                                         R (&h)[5]) {
     // m = M d (Eq. 9-11), as a deviation from the rest moments
     const R a = (d[1] + d[2]) + (d[3] + d[4]);

@@ -84,6 +84,28 @@ cudaError_t launch_step(const StepLaunch& L, const CoefSet& cs);
 cudaError_t launch_observe(const ObserveLaunch& L, const CoefSet& cs);
 cudaError_t launch_nusselt(const ObserveLaunch& L, const CoefSet& cs);
 cudaError_t launch_read_state(const ReadStateLaunch& L, const CoefSet& cs);
+// One reverse sweep of the discrete adjoint (lbm_adjoint.cu).  ckpt holds the
+// states B_{sK-1} for every segment s (slot 0: the rest state), seg has room
+// for K - 1 recomputed states, madj for two adjoint lattices (14 planes in the
+// arithmetic type), gphi one double per node.
+struct AdjointJob {
+    int precision;
+    Geom gm;
+    const void* coef;  // Coef<R> of the arithmetic type
+    long nsteps, ckpt_every;
+    size_t buf_bytes;
+    const void* ckpt;
+    void* seg;
+    void* madj;
+    double* gphi;
+    const void* phi;
+    int* status;
+    double L, dT;
+    void* out;  // ny*nx dense, double (FP64) or float (FP32)
+    cudaStream_t stream;
+};
+cudaError_t launch_adjoint_sweep(const AdjointJob& J);
+
 // Bytes of one state buffer (9 flow + 5 thermal planes) and of a porosity field.
 size_t state_buffer_bytes(int precision, int plane);
 size_t phi_bytes(int precision, int plane);

@@ -111,6 +111,16 @@ class Cavity:
                    umax=obs.umax, mass=obs.mass, heat=obs.heat, status=obs.status)
         return out
 
+    def adjoint(self, nsteps: int, ckpt_every: int = 100):
+        """(J, dJ/dphi): J = mean Nu of the hot wall after nsteps from the
+        initial state, and its gradient with respect to the porosity field,
+        as a (ny, nx) tensor.  Leaves the cavity at t = nsteps."""
+        out = torch.empty((self.ny, self.nx), dtype=self.field_dtype, device=self.device)
+        J = C.c_double()
+        L.check(L.load().lbm_adjoint_step(self._h, int(nsteps), int(ckpt_every), C.byref(J),
+                                          C.c_void_p(out.data_ptr())), self._h)
+        return J.value, out
+
     def nusselt(self):
         """(Nu of the hot wall, Nu of the cold wall), FP64 (Eq. 38)."""
         a, b = C.c_double(), C.c_double()

@@ -1,0 +1,96 @@
+"""Discrete adjoint (lbm_adjoint_step): dJ/dphi of the hot-wall mean Nusselt
+number against central differences of the FP64 oracle, on single cells of
+every kind (hot wall, corner, adiabatic wall, next to walls, interior, cold
+wall) and along random directions."""
+import numpy as np
+import pytest
+
+from oracle import Oracle, derive
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, N, K = 40, 36, 300, 64
+RA, DA, PHIBAR = 1e5, 1e-2, 0.6
+CELLS = [(0, 10), (1, 10), (2, 17), (3, 3), (1, 1), (0, 0), (1, 0), (4, 35), (5, 18), (10, 18), (20, 18),
+         (38, 18), (39, 18), (6, 2), (2, 6), (15, 30)]
+
+
+@pytest.fixture(scope="module")
+def phi():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    return perturbed_porosity(NY, NX, phi_bar=PHIBAR, amplitude=0.05, corr_len=6.0, seed=11)
+
+
+def j_oracle(phi, nthreads):
+    o = Oracle(derive(NX, NY, Ra=RA, Da=DA, phi=PHIBAR), phi_field=phi).step(N, threads=nthreads)
+    return o.nusselt()[0]
+
+
+@pytest.fixture(scope="module")
+def finite_differences(phi, nthreads):
+    fd = []
+    for (x, y) in CELLS:
+        h = 1e-5 * phi[y, x]
+        p = phi.copy()
+        p[y, x] += h
+        jp = j_oracle(p, nthreads)
+        p[y, x] -= 2 * h
+        jm = j_oracle(p, nthreads)
+        fd.append((jp - jm) / (2 * h))
+    rng = np.random.default_rng(5)
+    dirs = []
+    for _ in range(2):
+        v = rng.standard_normal(phi.shape)
+        v /= np.linalg.norm(v)
+        h = 1e-5
+        fd.append((j_oracle(phi + h * v, nthreads) - j_oracle(phi - h * v, nthreads)) / (2 * h))
+        dirs.append(v)
+    return np.array(fd), dirs, j_oracle(phi, nthreads)
+
+
+@pytest.mark.parametrize("precision,tol,tol_j", [("f64", 1e-6, 1e-10), ("f32", 1e-3, 1e-4)])
+def test_adjoint_matches_oracle_central_differences(phi, finite_differences, precision, tol, tol_j):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    fd, dirs, j0 = finite_differences
+    cav = Cavity(NX, NY, Ra=RA, Da=DA, phi=PHIBAR, precision=precision, phi_field=torch.from_numpy(phi).cuda())
+    J, g = cav.adjoint(N, K)
+    assert abs(J - j0) <= tol_j * abs(j0)
+    assert cav.query()[0] == N and abs(cav.nusselt()[0] - J) <= 1e-12 * abs(J)
+    g = g.double().cpu().numpy()
+    ad = [g[y, x] for (x, y) in CELLS] + [float((g * v).sum()) for v in dirs]
+    ad = np.array(ad)
+    err = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
+    assert err < tol, (err, list(zip(ad, fd)))
+    cav.close()
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(phi):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    grads = []
+    for k in (1, 7, 64, 1000):
+        cav = Cavity(NX, NY, Ra=RA, Da=DA, phi=PHIBAR, precision="f64", phi_field=torch.from_numpy(phi).cuda())
+        grads.append(cav.adjoint(120, k)[1].cpu().numpy())
+        cav.close()
+    for g in grads[1:]:
+        assert np.array_equal(g, grads[0])
+
+
+def test_adjoint_requires_a_porosity_field():
+    from paper_1308_2071_gb300 import Cavity, _lib
+
+    cav = Cavity(20, 20, Ra=1e4, Da=1e-2, phi=0.6, precision="f32")
+    with pytest.raises(_lib.LbmError, match="STATE"):
+        cav.adjoint(10, 5)
+    cav.close()
