@@ -146,13 +146,19 @@ def max_over_ranks(x, world):
 
 # ---- legs ----------------------------------------------------------------------------
 
-def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=True):
+TUNE_CACHE = os.path.join(ROOT, "paper_1308_2071_gb300", "_build", "tune_cache.txt")
+
+
+def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=True, shapes=None):
     import torch
 
     from paper_1308_2071_gb300 import Cavity
 
     w = workload(n)
     cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=precision, Pr=w["Pr"], Ma=w["Ma"])
+    shape = cav.tune(TUNE_CACHE)  # the library's autotuner (cached per lattice); resets to t = 0
+    if shapes is not None:
+        shapes[precision] = dict(block=[shape[0], shape[1]], nodes_per_thread=shape[2])
     cav.step(warmup)
     torch.cuda.synchronize()
     barrier(world)
@@ -223,8 +229,7 @@ def batched_leg(steps, warmup, ncav=256, seed=2071):
     cavs = cavity_sweep(ncav, seed=seed)
     nodes = sum(c["nx"] * c["ny"] for c in cavs)
     b = Batch(cavs, precision="f32")
-    cache = os.path.join(ROOT, "paper_1308_2071_gb300", "_build", "tune_cache.txt")
-    tw, th, bps = b.tune(cache)
+    tw, th, bps = b.tune(TUNE_CACHE)
     b.step(warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -316,7 +321,8 @@ def main():
     from paper_1308_2071_gb300 import _lib
 
     _lib.load()
-    ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local)
+    shapes = {}
+    ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local, shapes=shapes)
     ms = max_over_ranks(ms, world)
     nodes = a.size * a.size
     mlups = world * nodes * a.steps / (ms * 1e-3) / 1e6
@@ -331,7 +337,7 @@ def main():
                 vs_baseline=None, dtype=DTYPE[a.precision], data="synthetic (seeded, no dataset)",
                 config=dict(w, parallelism="replicas" if world > 1 else "single GPU",
                             global_batch=world, seq_len=None),
-                roofline=roof, clocks=clocks, gpu_launches=a.steps,
+                roofline=roof, clocks=clocks, gpu_launches=a.steps, launch_shape=shapes.get(a.precision),
                 nu_hot_at_end=obs["nu_hot"], status=obs["status"])
     if rank == 0 and not a.no_extras:
         variants = {}
@@ -340,11 +346,12 @@ def main():
         nsteps_cmp = a.warmup + k
         for prec in ("f64", "f16"):
             ms_p, obs_p, _ = device_leg(a.size, prec, k, a.warmup, 1, gpu_index=local,
-                                        sample_clocks=False)
+                                        sample_clocks=False, shapes=shapes)
             ach = nodes * BYTES_PER_NODE[prec] / (ms_p * 1e-3 / k) / 1e9
             variants[prec] = dict(mlups=round(nodes * k / (ms_p * 1e-3) / 1e6, 2),
                                   hbm_gbs=round(ach, 1), hbm_frac=round(ach / peak, 4), steps=k,
-                                  nu_hot=obs_p["nu_hot"], nu_cold=obs_p["nu_cold"], at_step=nsteps_cmp)
+                                  nu_hot=obs_p["nu_hot"], nu_cold=obs_p["nu_cold"], at_step=nsteps_cmp,
+                                  launch_shape=shapes.get(prec))
         _, obs32, _ = device_leg(a.size, "f32", k, a.warmup, 1, gpu_index=local, sample_clocks=False)
         nu64 = variants["f64"]["nu_hot"]
         variants["f32"] = dict(nu_hot=obs32["nu_hot"], at_step=nsteps_cmp)

@@ -69,6 +69,7 @@ typedef struct {
     int adiabatic_order; /* 1: T_b = T_f on adiabatic walls; 2: T_b = (4T_f - T_ff)/3   */
     int collision;       /* LBM_MRT or LBM_LBGK                                          */
     int block_x, block_y;/* launch shape of the step kernel; 0 = library default        */
+    int nodes_per_thread;/* 1 or 2 nodes per thread along y; 0 = library default        */
 } lbm_params;
 
 /* Observables of the post-stream state at the current time t (the state the
@@ -111,6 +112,14 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out);
  * use_phi_field = 1.  Resets the state to the initial state (t = 0).
  * Errors: LBM_ERR_ARG, LBM_ERR_STATE (use_phi_field = 0), LBM_ERR_CUDA. */
 int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype);
+
+/* Autotuner of the step kernel: times candidate launch shapes (block_x x
+ * block_y threads, 1 or 2 nodes per thread) on this lattice, keeps the
+ * fastest and records it in a text cache at cache_path (NULL: no cache; one
+ * line per device, precision, lattice size and porosity mode); a cached entry
+ * is reused without timing.  Timing advances the lattice, so the handle is
+ * reset to its initial state (t = 0) afterwards.  Outputs may be NULL. */
+int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, int* nodes_per_thread);
 
 /* Advances nsteps time steps of Eq. 17-18 and Eq. 34-35 with the wall rule
  * (Section 4), asynchronously on the handle's stream.  Long runs replay a

@@ -40,7 +40,7 @@ struct lbm_handle_s {
     double* obs_host = nullptr;
     int* status_dev = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int bx = 128, by = 2;
+    int bx = 128, by = 2, npt = 1;
     std::string err;
 };
 
@@ -198,6 +198,7 @@ StepLaunch step_launch(lbm_handle h, int src, cudaStream_t s) {
     L.gm = h->gm;
     L.bx = h->bx;
     L.by = h->by;
+    L.npt = h->npt;
     L.status = h->status_dev;
     L.stream = s;
     return L;
@@ -292,9 +293,11 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     const long plane = h->gm.plane;
     h->bx = p->block_x > 0 ? p->block_x : (p->nx <= 64 ? 64 : 128);
     h->by = p->block_y > 0 ? p->block_y : 256 / h->bx;
-    if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0) {
+    // FP16-flow lattices move 38 B per node each way: two nodes per thread by default
+    h->npt = p->nodes_per_thread > 0 ? p->nodes_per_thread : (p->precision == LBM_F32_STORE_F16 ? 2 : 1);
+    if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0 || h->npt > 2) {
         delete h;
-        return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256");
+        return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256 and nodes_per_thread 1 or 2");
     }
     h->stream = (cudaStream_t)stream;
     h->buf_bytes = state_buffer_bytes(p->precision, (int)plane);
@@ -363,6 +366,90 @@ int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype) {
     CK(h, launch_convert_phi(phi_dev, dtype == LBM_F64, h->phi, h->precision, h->gm, kReduceBlocks, h->stream));
     drop_graphs(h);
     return reset_state(h);
+}
+
+int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, int* nodes_per_thread) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    char sig[256];
+    {
+        int dev = 0;
+        cudaDeviceProp pr;
+        std::string name = "unknown";
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&pr, dev) == cudaSuccess) name = pr.name;
+        for (auto& ch : name)
+            if (ch == ' ') ch = '_';
+        snprintf(sig, sizeof sig, "step:%s:p%d:%dx%d:f%d", name.c_str(), h->precision, h->p.nx, h->p.ny,
+                 h->p.use_phi_field);
+    }
+    int best[3] = {h->bx, h->by, h->npt};
+    bool cached = false;
+    if (cache_path) {
+        FILE* fp = fopen(cache_path, "r");
+        if (fp) {
+            char key[256];
+            int a, b, c;
+            while (fscanf(fp, "%255s %d %d %d", key, &a, &b, &c) == 4)
+                if (strcmp(key, sig) == 0) {
+                    best[0] = a;
+                    best[1] = b;
+                    best[2] = c;
+                    cached = true;
+                }
+            fclose(fp);
+        }
+    }
+    if (!cached) {
+        const int cand[][3] = {{128, 2, 1}, {64, 4, 1}, {256, 1, 1}, {32, 8, 1}, {128, 1, 2},
+                               {64, 2, 2},  {128, 2, 2}, {256, 1, 2}, {32, 4, 2}};
+        cudaEvent_t e0, e1;
+        CK(h, cudaEventCreate(&e0));
+        CK(h, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        drop_graphs(h);
+        for (auto& cd : cand) {
+            h->bx = cd[0];
+            h->by = cd[1];
+            h->npt = cd[2];
+            for (int k = 0; k < 3; ++k) {
+                CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
+                h->cur ^= 1;
+            }
+            CK(h, cudaEventRecord(e0, h->stream));
+            for (int k = 0; k < 30; ++k) {
+                CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
+                h->cur ^= 1;
+            }
+            CK(h, cudaEventRecord(e1, h->stream));
+            CK(h, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best[0] = cd[0];
+                best[1] = cd[1];
+                best[2] = cd[2];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cache_path) {
+            FILE* fp = fopen(cache_path, "a");
+            if (fp) {
+                fprintf(fp, "%s %d %d %d\n", sig, best[0], best[1], best[2]);
+                fclose(fp);
+            }
+        }
+    }
+    h->bx = best[0];
+    h->by = best[1];
+    h->npt = best[2];
+    drop_graphs(h);
+    int rc = reset_state(h);
+    if (rc != LBM_OK) return rc;
+    if (block_x) *block_x = best[0];
+    if (block_y) *block_y = best[1];
+    if (nodes_per_thread) *nodes_per_thread = best[2];
+    return LBM_OK;
 }
 
 int lbm_step(lbm_handle h, long nsteps) {

@@ -50,6 +50,7 @@ struct StepLaunch {
     const void* phi;  // per-cell porosity in the storage type, or nullptr
     Geom gm;
     int bx, by;
+    int npt = 1;  // nodes per thread along y (1 or 2)
     int* status;
     cudaStream_t stream;
 };

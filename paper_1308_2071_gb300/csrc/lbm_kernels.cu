@@ -31,6 +31,57 @@ __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const type
     for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
 }
 
+// Two nodes per thread, (x, y) and (x, y + blockDim.y): when both are fluid
+// nodes all 28 loads are issued before any arithmetic, doubling the bytes in
+// flight per thread (the FP16-flow variant moves 38 B per node, too few to
+// cover HBM latency with one node per thread).  Wall nodes take the general
+// path one at a time.
+template <class T, bool FIELD>
+__global__ void __launch_bounds__(256) k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
+                                               Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+    using R = typename T::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y0 = blockIdx.y * (2 * blockDim.y) + threadIdx.y;
+    const int y1 = y0 + blockDim.y;
+    if (x >= gm.nx || y0 >= gm.ny) return;
+    const bool fluid_x = x > 0 && x < gm.nx - 1;
+    R d0[9], h0[5], d1[9], h1[5];
+    if (fluid_x && y0 > 0 && y1 < gm.ny - 1) {
+        const int off0 = y0 * gm.pitch + x, off1 = y1 * gm.pitch + x;
+        pull<T>(src, gm, off0, d0, h0);
+        pull<T>(src, gm, off1, d1, h1);
+        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
+        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
+        const Macro<R> m0 = fluid_macros<R>(c, dr0, d0, h0);
+        const Macro<R> m1 = fluid_macros<R>(c, dr1, d1, h1);
+        if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
+        collide<R>(c, dr0.iphi, m0, d0, h0);
+        collide<R>(c, dr1.iphi, m1, d1, h1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
+            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off1, d1[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
+            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
+        }
+        return;
+    }
+    for (int y = y0; y <= y1 && y < gm.ny; y += blockDim.y) {
+        Drag<R> dr;
+        const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d0, h0);
+        if (!(mc.umag < R(0.5))) atomicOr(status, 1);
+        collide<R>(c, dr.iphi, mc, d0, h0);
+        const int off = y * gm.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d0[i]);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h0[j]);
+    }
+}
+
 // ---- observables ------------------------------------------------------------------
 
 // Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).
@@ -199,9 +250,18 @@ template <> const Coef<float>& coef_of<PrecF16>(const CoefSet& cs) { return cs.f
 template <class T>
 static cudaError_t launch_step_t(const StepLaunch& L, const CoefSet& cs) {
     dim3 blk(L.bx, L.by);
-    dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
     const Src<T> s = src_view<T>(L.src, L.gm.plane);
     const Dst<T> d = dst_view<T>(L.dst, L.gm.plane);
+    if (L.npt == 2) {
+        dim3 grd2((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + 2 * L.by - 1) / (2 * L.by));
+        if (L.phi)
+            k_step2<T, true><<<grd2, blk, 0, L.stream>>>(s, d, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
+                                                        L.status);
+        else
+            k_step2<T, false><<<grd2, blk, 0, L.stream>>>(s, d, nullptr, L.gm, coef_of<T>(cs), L.status);
+        return cudaGetLastError();
+    }
+    dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
     if (L.phi)
         k_step<T, true><<<grd, blk, 0, L.stream>>>(s, d, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
                                                   L.status);

@@ -89,6 +89,14 @@ class Cavity:
         self._sync_inputs(phi)
         L.check(L.load().lbm_set_porous_field(self._h, C.c_void_p(phi.data_ptr()), dt), self._h)
 
+    def tune(self, cache_path: str | None = None):
+        """Picks the fastest launch shape for this lattice (resets to t = 0);
+        returns (block_x, block_y, nodes_per_thread)."""
+        bx, by, npt = C.c_int(), C.c_int(), C.c_int()
+        path = cache_path.encode() if cache_path else None
+        L.check(L.load().lbm_tune(self._h, path, C.byref(bx), C.byref(by), C.byref(npt)), self._h)
+        return bx.value, by.value, npt.value
+
     def step(self, n: int = 1) -> "Cavity":
         L.check(L.load().lbm_step(self._h, int(n)), self._h)
         return self
