@@ -229,12 +229,18 @@ int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev);
  * grid barrier before it records LBM_ERR_TIMEOUT and leaves the kernel;
  * default 2e7.  Also clears a previous timeout. */
 int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
-/* Autotuner: times candidate tile shapes (tile_w x tile_h nodes) and blocks
- * per SM on this batch, keeps the fastest, and records it in a text cache
+/* Autotuner: times candidate tile shapes (tile_w x tile_h nodes), blocks per
+ * SM and the two scheduling modes on this batch, keeps the fastest, and records it in a text cache
  * (one line per device, precision and batch shape) at cache_path (NULL: no
  * cache); a cached entry is reused without timing.  Tuning advances the
  * lattices, so the batch is reset to t = 0 afterwards.  Outputs may be NULL. */
 int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm);
+/* Sets the tile shape (tile_w a power of two, tile_w x tile_h = 256 nodes: one
+ * node per thread, or 512: two), blocks per SM (0 = as many as fit) and the
+ * scheduling (dynamic = 0: each block owns a contiguous run of tiles;
+ * 1: blocks take chunks of 4 tiles from a per-step counter) without timing;
+ * resets the batch to t = 0. */
+int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic);
 /* Steps taken, number of tiles and blocks of the persistent launch. */
 int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks);
 int lbm_batch_destroy(lbm_batch b);

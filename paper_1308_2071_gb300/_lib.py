@@ -66,6 +66,7 @@ SIGNATURES = [
     ("lbm_batch_set_wait_limit", C.c_int, [C.c_void_p, C.c_longlong]),
     ("lbm_batch_tune", C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_int)]),
+    ("lbm_batch_set_tiles", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     ("lbm_batch_query", C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lbm_batch_destroy", C.c_int, [C.c_void_p]),
     ("lbm_batch_last_error", C.c_char_p, [C.c_void_p]),

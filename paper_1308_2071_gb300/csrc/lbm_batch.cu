@@ -36,7 +36,7 @@ struct Tile {
 // to change, at most `limit` polls of ~0.1-1 us each.  Returns false (in every
 // thread of the block) when the wait ran out.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
-                                             long long limit, int* flag) {
+                                             long long limit, int* flag, int* reset_on_release) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -46,6 +46,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
         const unsigned arrived = atomicAdd(count, 1u);
         if (arrived == nblocks - 1) {
             atomicExch(count, 0u);
+            if (reset_on_release) atomicExch(reset_on_release, 0);
             __threadfence();
             atomicAdd((unsigned*)gen, 1u);
         } else {
@@ -68,53 +69,69 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
 
 // One launch runs `nsteps` steps of every cavity.  Buffer parity `par` of
 // every cavity holds B_n on entry.
-template <class T>
-__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 2) k_batch(const CavDesc<typename T::R>* __restrict__ cavs,
-                                               const Tile* __restrict__ tiles, int ntiles, int tw, int th,
+template <class T, int NPT>
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 4 : 3) : 2)
+    k_batch(const CavDesc<typename T::R>* __restrict__ cavs, const Tile* __restrict__ tiles, int ntiles, int lg_tw,
+            int dyn, int* __restrict__ tile_ctr,
                                                long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
                                                long long wait_limit, int* __restrict__ status,
                                                int* __restrict__ timeout_flag) {
     using R = typename T::R;
     __shared__ CavDesc<R> cd;
-    // each block owns a contiguous run of tiles (row-major within a cavity), so
-    // the cavity changes rarely and only then does the block synchronise
+    __shared__ int chunk_sh;
+    constexpr int kChunk = 4;
+    // static mode: each block owns a contiguous run of tiles (row-major within a
+    // cavity); dynamic mode: blocks take chunks of kChunk tiles from a per-step
+    // counter.  Either way the block restages the descriptor only when the
+    // cavity changes.
     const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int t0 = blockIdx.x * per, t1 = min(ntiles, t0 + per);
     for (long s = 0; s < nsteps; ++s) {
         int cur_cav = -1;
-        for (int t = t0; t < t1; ++t) {
-            const Tile tl = tiles[t];
-            if (tl.cav != cur_cav) {  // block-uniform branch
+        int t0 = blockIdx.x * per, t1 = min(ntiles, t0 + per);
+        for (;;) {
+            if (dyn) {
                 __syncthreads();
-                const int* srcw = (const int*)&cavs[tl.cav];
-                int* dstw = (int*)&cd;
-                for (int k = threadIdx.x; k < (int)(sizeof(CavDesc<R>) / sizeof(int)); k += blockDim.x)
-                    dstw[k] = srcw[k];
+                if (threadIdx.x == 0) chunk_sh = atomicAdd(&tile_ctr[s & 1], kChunk);
                 __syncthreads();
-                cur_cav = tl.cav;
+                t0 = chunk_sh;
+                t1 = min(ntiles, t0 + kChunk);
             }
-            const Geom gm = cd.gm;
-            const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
-            const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
-            for (int k = threadIdx.x; k < tw * th; k += blockDim.x) {
-                const int x = tl.x0 + k % tw, y = tl.y0 + k / tw;
-                if (x >= gm.nx || y >= gm.ny) continue;
-                R d[9], h[5];
-                Drag<R> dr;
-                const Macro<R> mc = node_state<T, false>(cd.c, gm, src, nullptr, x, y, dr, d, h);
-                if (!(mc.umag < R(0.5))) atomicOr(&status[tl.cav], 1);
-                collide<R>(cd.c, dr.iphi, mc, d, h);
-                const int off = y * gm.pitch + x;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
-#pragma unroll
-                for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+            if (t0 >= t1) break;
+            for (int t = t0; t < t1; ++t) {
+                const Tile tl = tiles[t];
+                if (tl.cav != cur_cav) {  // block-uniform branch
+                    __syncthreads();
+                    const int* srcw = (const int*)&cavs[tl.cav];
+                    int* dstw = (int*)&cd;
+                    for (int k = threadIdx.x; k < (int)(sizeof(CavDesc<R>) / sizeof(int)); k += blockDim.x)
+                        dstw[k] = srcw[k];
+                    __syncthreads();
+                    cur_cav = tl.cav;
+                }
+                const Geom gm = cd.gm;
+                const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
+                const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
+                // tiles hold 256 * NPT nodes, tile width 2^lg_tw
+                const int msk = (1 << lg_tw) - 1;
+                if constexpr (NPT == 2) {
+                    const int k0 = threadIdx.x, k1 = threadIdx.x + 256;
+                    const int x0 = tl.x0 + (k0 & msk), y0 = tl.y0 + (k0 >> lg_tw);
+                    const int x1 = tl.x0 + (k1 & msk), y1 = tl.y0 + (k1 >> lg_tw);
+                    update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
+                                          x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
+                } else {
+                    const int x = tl.x0 + (threadIdx.x & msk), y = tl.y0 + (threadIdx.x >> lg_tw);
+                    if (x < gm.nx && y < gm.ny)
+                        update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
+                }
             }
+            if (!dyn) break;
         }
         par ^= 1;
         if (s + 1 < nsteps) {
             __threadfence();
-            if (!grid_barrier(bar_count, bar_gen, gridDim.x, wait_limit, timeout_flag)) return;
+            // the releasing block clears the counter of step s + 1 (used two steps ago)
+            if (!grid_barrier(bar_count, bar_gen, gridDim.x, wait_limit, timeout_flag, &tile_ctr[(s + 1) & 1])) return;
         }
     }
 }
@@ -175,7 +192,7 @@ namespace {
 constexpr long long kDefaultWaitPolls = 20000000;  // ~2-20 s of 100 ns polls
 
 struct TuneChoice {
-    int tw = 128, th = 2, blocks_per_sm = 0;
+    int tw = 128, th = 2, blocks_per_sm = 0, dyn = 0;
 };
 
 }  // namespace
@@ -198,6 +215,7 @@ struct lbm_batch_s {
     int* status = nullptr;  // per cavity
     int* timeout_flag = nullptr;
     unsigned* bar = nullptr;  // count, gen
+    int* tile_ctr = nullptr;  // dynamic scheduling: one counter per step parity
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int par = 0;  // parity holding B_n
@@ -227,7 +245,17 @@ int bfail(lbm_batch b, int code, const std::string& m) {
         if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-template <class T> const void* kernel_ptr() { return (const void*)&k_batch<T>; }
+template <class T> const void* kernel_ptr(int npt) {
+    return npt == 2 ? (const void*)&k_batch<T, 2> : (const void*)&k_batch<T, 1>;
+}
+
+int npt_of(const TuneChoice& t) { return t.tw * t.th == 512 ? 2 : 1; }
+
+int log2i(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
 
 int build_tiles(lbm_batch b) {
     if (b->stream) BCK(b, cudaStreamSynchronize(b->stream));  // queued launches may still read the old list
@@ -247,7 +275,7 @@ int grid_size(lbm_batch b, int* nblocks) {
     int dev = 0, nsm = 0, per_sm = 0;
     BCK(b, cudaGetDevice(&dev));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>() : kernel_ptr<PrecF32P>();
+    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt_of(b->tune)) : kernel_ptr<PrecF32P>(npt_of(b->tune));
     BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
     if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "batched kernel cannot be resident");
     int want = b->tune.blocks_per_sm > 0 ? std::min(b->tune.blocks_per_sm, per_sm) : per_sm;
@@ -256,28 +284,33 @@ int grid_size(lbm_batch b, int* nblocks) {
 }
 
 int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
-    void* args[13];
+    void* args[14];
     long ns = nsteps;
     int pr = par;
     unsigned* cnt = b->bar;
     unsigned* gen = b->bar + 1;
     long long lim = b->wait_limit;
-    int tw = b->tune.tw, th = b->tune.th, nt = b->ntiles;
+    int lg = log2i(b->tune.tw), nt = b->ntiles;
     const void* descs = b->descs;
     const Tile* tiles = b->tiles;
+    int dyn = b->tune.dyn;
     args[0] = &descs;
     args[1] = &tiles;
     args[2] = &nt;
-    args[3] = &tw;
-    args[4] = &th;
-    args[5] = &ns;
-    args[6] = &pr;
-    args[7] = &cnt;
-    args[8] = &gen;
-    args[9] = &lim;
-    args[10] = &b->status;
-    args[11] = &b->timeout_flag;
-    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>() : kernel_ptr<PrecF32P>();
+    args[3] = &lg;
+    args[4] = &dyn;
+    args[5] = &b->tile_ctr;
+    args[6] = &ns;
+    args[7] = &pr;
+    args[8] = &cnt;
+    args[9] = &gen;
+    args[10] = &lim;
+    args[11] = &b->status;
+    args[12] = &b->timeout_flag;
+    cudaError_t ez = cudaMemsetAsync(b->tile_ctr, 0, 2 * sizeof(int), s);
+    if (ez != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("counter reset: ") + cudaGetErrorString(ez));
+    const int npt = npt_of(b->tune);
+    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt) : kernel_ptr<PrecF32P>(npt);
     cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(256), args, 0, s);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
     return LBM_OK;
@@ -360,7 +393,7 @@ bool cache_lookup(const std::string& path, const std::string& sig, TuneChoice* t
         std::istringstream ss(line);
         std::string key;
         TuneChoice t;
-        if (ss >> key >> t.tw >> t.th >> t.blocks_per_sm && key == sig) {
+        if (ss >> key >> t.tw >> t.th >> t.blocks_per_sm >> t.dyn && key == sig) {
             *tc = t;
             return true;
         }
@@ -370,7 +403,7 @@ bool cache_lookup(const std::string& path, const std::string& sig, TuneChoice* t
 
 void cache_store(const std::string& path, const std::string& sig, const TuneChoice& tc) {
     std::ofstream out(path, std::ios::app);
-    if (out) out << sig << " " << tc.tw << " " << tc.th << " " << tc.blocks_per_sm << "\n";
+    if (out) out << sig << " " << tc.tw << " " << tc.th << " " << tc.blocks_per_sm << " " << tc.dyn << "\n";
 }
 
 }  // namespace
@@ -436,6 +469,7 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
     BI(cudaMalloc(&b->status, sizeof(int) * ncav));
     BI(cudaMalloc(&b->timeout_flag, sizeof(int)));
     BI(cudaMalloc(&b->bar, 2 * sizeof(unsigned)));
+    BI(cudaMalloc(&b->tile_ctr, 2 * sizeof(int)));
     BI(cudaMalloc(&b->Ls, sizeof(double) * 2 * ncav));
     BI(cudaMalloc(&b->nu_dev, sizeof(double) * 2 * ncav));
 #undef BI
@@ -536,17 +570,19 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);
     if (!cached) {
         const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1}};
-        const int occ[] = {0, 4, 2};
+        const int occ[] = {0, 2};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         BCK(b, cudaEventCreate(&e0));
         BCK(b, cudaEventCreate(&e1));
         const long nsteps = 20;
         for (auto& sh : shapes)
-            for (int o : occ) {
+            for (int o : occ)
+            for (int dyn = 0; dyn < 2; ++dyn) {
                 b->tune.tw = sh[0];
                 b->tune.th = sh[1];
                 b->tune.blocks_per_sm = o;
+                b->tune.dyn = dyn;
                 int rc = build_tiles(b);
                 if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
                 drop_graph(b);
@@ -580,6 +616,22 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     return LBM_OK;
 }
 
+int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (tile_w <= 0 || tile_h <= 0 || (tile_w * tile_h != 256 && tile_w * tile_h != 512) ||
+        (tile_w & (tile_w - 1)) != 0 || blocks_per_sm < 0)
+        return bfail(b, LBM_ERR_ARG, "tiles hold 256 or 512 nodes and have a power-of-two width");
+    b->tune.tw = tile_w;
+    b->tune.th = tile_h;
+    b->tune.blocks_per_sm = blocks_per_sm;
+    b->tune.dyn = dynamic ? 1 : 0;
+    int rc = build_tiles(b);
+    if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
+    drop_graph(b);
+    if (rc == LBM_OK) rc = reset(b);
+    return rc;
+}
+
 int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     if (t) *t = b->t;
@@ -600,6 +652,7 @@ int lbm_batch_destroy(lbm_batch b) {
     if (b->status) cudaFree(b->status);
     if (b->timeout_flag) cudaFree(b->timeout_flag);
     if (b->bar) cudaFree(b->bar);
+    if (b->tile_ctr) cudaFree(b->tile_ctr);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return LBM_OK;

@@ -426,6 +426,62 @@ __device__ __forceinline__ Macro<typename T::R> node_state(const Coef<typename T
     return wall_node<T, FIELD>(c, gm, src, phi_field, x, y, nr, dr, d, h);
 }
 
+// One node of the step: pull (or wall rule), collide, store.
+template <class T, bool FIELD>
+__device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
+                                            const Dst<T>& dst, const typename T::P* phi, int x, int y,
+                                            int* status) {
+    using R = typename T::R;
+    R d[9], h[5];
+    Drag<R> dr;
+    const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
+    if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
+    collide<R>(c, dr.iphi, mc, d, h);
+    const int off = y * gm.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+}
+
+// Two nodes at once: when both are fluid nodes all 28 loads are issued before
+// any arithmetic (twice the bytes in flight of one node per thread); nodes
+// outside the lattice (valid = false) or on walls take the one-node path.
+template <class T, bool FIELD>
+__device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
+                                            const Dst<T>& dst, const typename T::P* phi, int x0, int y0,
+                                            bool v0, int x1, int y1, bool v1, int* status) {
+    using R = typename T::R;
+    const bool f0 = v0 && x0 > 0 && x0 < gm.nx - 1 && y0 > 0 && y0 < gm.ny - 1;
+    const bool f1 = v1 && x1 > 0 && x1 < gm.nx - 1 && y1 > 0 && y1 < gm.ny - 1;
+    if (f0 && f1) {
+        R d0[9], h0[5], d1[9], h1[5];
+        const int off0 = y0 * gm.pitch + x0, off1 = y1 * gm.pitch + x1;
+        pull<T>(src, gm, off0, d0, h0);
+        pull<T>(src, gm, off1, d1, h1);
+        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
+        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
+        const Macro<R> m0 = fluid_macros<R>(c, dr0, d0, h0);
+        const Macro<R> m1 = fluid_macros<R>(c, dr1, d1, h1);
+        if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
+        collide<R>(c, dr0.iphi, m0, d0, h0);
+        collide<R>(c, dr1.iphi, m1, d1, h1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
+            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off1, d1[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
+            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
+        }
+        return;
+    }
+    if (v0) update_node<T, FIELD>(c, gm, src, dst, phi, x0, y0, status);
+    if (v1) update_node<T, FIELD>(c, gm, src, dst, phi, x1, y1, status);
+}
+
 // T - T0 of the post-stream state at node (x, y), pulled from B_{n-1}
 // (the wall rule's temperature on wall nodes).
 template <class T>

@@ -15,20 +15,10 @@ namespace lbm {
 template <class T, bool FIELD>
 __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
                                               Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
-    using R = typename T::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= gm.nx || y >= gm.ny) return;
-    R d[9], h[5];
-    Drag<R> dr;
-    const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
-    if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
-    collide<R>(c, dr.iphi, mc, d, h);
-    const int off = y * gm.pitch + x;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+    update_node<T, FIELD>(c, gm, src, dst, phi, x, y, status);
 }
 
 // Two nodes per thread, (x, y) and (x, y + blockDim.y): when both are fluid
@@ -39,47 +29,11 @@ __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const type
 template <class T, bool FIELD>
 __global__ void __launch_bounds__(256) k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
                                                Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
-    using R = typename T::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y0 = blockIdx.y * (2 * blockDim.y) + threadIdx.y;
     const int y1 = y0 + blockDim.y;
     if (x >= gm.nx || y0 >= gm.ny) return;
-    const bool fluid_x = x > 0 && x < gm.nx - 1;
-    R d0[9], h0[5], d1[9], h1[5];
-    if (fluid_x && y0 > 0 && y1 < gm.ny - 1) {
-        const int off0 = y0 * gm.pitch + x, off1 = y1 * gm.pitch + x;
-        pull<T>(src, gm, off0, d0, h0);
-        pull<T>(src, gm, off1, d1, h1);
-        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
-        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
-        const Macro<R> m0 = fluid_macros<R>(c, dr0, d0, h0);
-        const Macro<R> m1 = fluid_macros<R>(c, dr1, d1, h1);
-        if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
-        collide<R>(c, dr0.iphi, m0, d0, h0);
-        collide<R>(c, dr1.iphi, m1, d1, h1);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
-            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off1, d1[i]);
-        }
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
-            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
-        }
-        return;
-    }
-    for (int y = y0; y <= y1 && y < gm.ny; y += blockDim.y) {
-        Drag<R> dr;
-        const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d0, h0);
-        if (!(mc.umag < R(0.5))) atomicOr(status, 1);
-        collide<R>(c, dr.iphi, mc, d0, h0);
-        const int off = y * gm.pitch + x;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d0[i]);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h0[j]);
-    }
+    update_pair<T, FIELD>(c, gm, src, dst, phi, x, y0, true, x, y1, y1 < gm.ny, status);
 }
 
 // ---- observables ------------------------------------------------------------------

@@ -247,6 +247,9 @@ class Batch:
         self._check(L.load().lbm_batch_tune(self._b, path, C.byref(tw), C.byref(th), C.byref(bps)))
         return tw.value, th.value, bps.value
 
+    def set_tiles(self, tile_w: int, tile_h: int, blocks_per_sm: int = 0, dynamic: bool = False):
+        self._check(L.load().lbm_batch_set_tiles(self._b, tile_w, tile_h, blocks_per_sm, int(dynamic)))
+
     def query(self):
         t, nt, nb = C.c_long(), C.c_int(), C.c_int()
         self._check(L.load().lbm_batch_query(self._b, C.byref(t), C.byref(nt), C.byref(nb)))

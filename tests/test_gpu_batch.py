@@ -52,11 +52,14 @@ def test_batch_matches_single_cavity_bit_for_bit():
     b.close()
 
 
-def test_batch_fp64_matches_oracle(nthreads):
+@pytest.mark.parametrize("tiles", [None, (64, 8, 0, False), (32, 8, 0, True), (128, 4, 2, True)])
+def test_batch_fp64_matches_oracle(nthreads, tiles):
     from paper_1308_2071_gb300 import Batch
 
     cavs = CAVS[:3]
     b = Batch(cavs, precision="f64")
+    if tiles:
+        b.set_tiles(*tiles)  # 512-node tiles: two nodes per thread
     b.step(250)
     hot, _ = b.nusselt()
     for k, cv in enumerate(cavs):
@@ -66,6 +69,22 @@ def test_batch_fp64_matches_oracle(nthreads):
         assert np.abs(np_(f) - fo).max() < 1e-12, k
         assert np.abs(np_(g) - go).max() < 1e-12, k
         assert abs(hot[k] - o.nusselt()[0]) < 1e-10 * abs(hot[k]), k
+    b.close()
+
+
+def test_two_node_tiles_agree_with_the_single_cavity_kernel():
+    from paper_1308_2071_gb300 import Batch, Cavity
+
+    b = Batch(CAVS, precision="f32")
+    b.set_tiles(32, 16)
+    b.step(300)
+    for k, cv in enumerate(CAVS):
+        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision="f32",
+                   nodes_per_thread=2)
+        c.step(300)
+        # same formulas; fused multiply-adds may differ: FP32 roundings over 300 steps
+        assert np.abs(np_(c.read_state()[0]) - np_(b.read_state(k)[0])).max() < 2e-6, k
+        c.close()
     b.close()
 
 
