@@ -275,6 +275,55 @@ def adjoint_leg(n=512, nsteps=2000, ckpt=100):
                 grad_l2=float(g.double().norm()))
 
 
+def heterogeneous_leg(n=8192, steps=1000, warmup=3):
+    """Config 3: n^2 cavity (Ra 1e5, Da 1e-4, mean porosity 0.6) with a seeded
+    porosity field whose permeability is log-normal (correlation length 32
+    cells, porosity clipped to [0.3, 0.9]); FP32 and FP16-flow storage against
+    the FP64 GPU path after the same steps: per-field errors and MLUPS."""
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+    from paper_1308_2071_gb300.inputs import porosity_field
+
+    t0 = time.perf_counter()
+    phi = torch.from_numpy(porosity_field(n, n, phi_bar=0.6, corr_len=32.0, seed=1308)).cuda()
+    gen_s = time.perf_counter() - t0
+    out = dict(workload=f"{n}x{n}, Ra 1e5, Da 1e-4, log-normal K field (corr. 32, seed 1308), {steps} steps",
+               field_seconds=round(gen_s, 1))
+    fields = {}
+    peak, _ = load_peaks()
+    for prec in ("f64", "f32", "f16"):
+        cav = Cavity(n, n, Ra=1e5, Da=1e-4, phi=0.6, precision=prec, phi_field=phi)
+        cav.tune(TUNE_CACHE)
+        cav.set_porous_field(phi)  # tuning reset to t = 0; this keeps the field and restarts
+        cav.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cav.stream)
+        cav.step(steps - warmup)
+        e1.record(cav.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        obs = cav.observables(fields=True)
+        bpn = BYTES_PER_NODE[prec] + (16 if prec == "f64" else 8) // 2  # + the porosity read
+        gbs = n * n * bpn / (ms * 1e-3 / (steps - warmup)) / 1e9
+        out[prec] = dict(mlups=round(n * n * (steps - warmup) / (ms * 1e-3) / 1e6, 2), hbm_gbs=round(gbs, 1),
+                         hbm_frac=round(gbs / peak, 4), nu_hot=obs["nu_hot"])
+        fields[prec] = {k: obs[k].double() for k in ("ux", "uy", "T")}
+        fields[prec]["nu"] = obs["nu_hot"]
+        cav.close()
+    ref = fields["f64"]
+    umax = float(torch.maximum(ref["ux"].abs().max(), ref["uy"].abs().max()))
+    for prec in ("f32", "f16"):
+        f = fields[prec]
+        out[prec]["err_u_rel_max"] = float(torch.maximum((f["ux"] - ref["ux"]).abs().max(),
+                                                         (f["uy"] - ref["uy"]).abs().max())) / umax
+        out[prec]["err_T_max_over_dT"] = float((f["T"] - ref["T"]).abs().max())
+        out[prec]["err_nu_rel"] = abs(f["nu"] - ref["nu"]) / abs(ref["nu"])
+    return out
+
+
 def cpu_leg(n, seconds, warmup=1, max_steps=None):
     """The FP64 oracle as it stands, on every host core, on a bounded number of
     steps of the same lattice; returns (MLUPS, threads, steps, seconds)."""
@@ -362,6 +411,7 @@ def main():
         line["e2e"] = e2e_leg(a.size, a.precision, min(a.steps, 1000))
         line["batched"] = batched_leg(min(a.steps, 1000), 8)
         line["adjoint"] = adjoint_leg()
+        line["heterogeneous"] = heterogeneous_leg()
         mlc, threads, k, dt = cpu_leg(a.size, a.cpu_seconds)
         line["cpu_baseline"] = dict(value=round(mlc, 3), unit="MLUPS", cores=threads, kind="oracle",
                                     sample=f"{k} steps of the {a.size}^2 lattice, FP64 oracle, {dt:.1f} s")

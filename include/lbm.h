@@ -53,7 +53,8 @@ extern "C" {
 /* Parameters of one cavity.  Physical inputs follow Section 2 (Ra, Da, Pr, J,
  * porosity), the lattice set-up follows Section 4: rho0 = 1, delta_t = 1,
  * Eq. 37 (second occurrence) for tau_nu and tau_T, U = sqrt(g beta dT L) =
- * Ma c_s, K = Da L^2, F_phi from Ergun's relation (Eq. 5). */
+ * Ma c_s, K = Da L^2 (Da = INFINITY: no Darcy or Forchheimer drag), F_phi
+ * from Ergun's relation (Eq. 5). */
 typedef struct {
     int nx, ny;          /* nodes including the wall nodes, both >= 5                 */
     double Ra, Da, Pr, J;
@@ -70,6 +71,10 @@ typedef struct {
     int collision;       /* LBM_MRT or LBM_LBGK                                          */
     int block_x, block_y;/* launch shape of the step kernel; 0 = library default        */
     int nodes_per_thread;/* 1 or 2 nodes per thread along y; 0 = library default        */
+    double RaI;          /* internal Rayleigh number (Section 2); 0 = none.  With
+                            LBM_BC_SIDE_HEATED: Q''' = (RaI/Ra) alpha_e (Th-Tc)/L^2
+                            (Section 4.3); with LBM_BC_COOLED: tau_nu from RaI,
+                            dT = Q''' L^2 / alpha_e := Th - Tc, T0 = Tc (Section 4.2) */
 } lbm_params;
 
 /* Observables of the post-stream state at the current time t (the state the
@@ -153,6 +158,21 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
  * current state, FP64; reads only the five node columns next to each wall.
  * Synchronises the stream. */
 int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold);
+
+/* Steady-state control loop run on the device: one CUDA graph whose
+ * conditional while-node repeats {check_every steps (rounded up to even),
+ * then a one-block check of both wall Nusselt numbers} until their relative
+ * change between two checks falls below tol, the divergence flag is raised,
+ * or max_steps is reached; the host waits once.  *steps_taken and *change
+ * (host, may be NULL) report the steps run and the last relative change.
+ * Returns LBM_ERR_DIVERGED if the flag was raised. */
+int lbm_run_steady(lbm_handle h, double tol, long check_every, long max_steps, long* steps_taken, double* change);
+
+/* Extrema for the validation tables: maximum temperature and the minimum and
+ * maximum of the stream function psi(x, y) = integral_0^y u_x dy' (trapezoidal
+ * along y, psi = 0 on the bottom wall; lattice units) of the current state.
+ * Host outputs may be NULL.  Synchronises. */
+int lbm_field_extrema(lbm_handle h, double* T_max, double* psi_min, double* psi_max);
 
 /* Writes the full post-stream populations of the current state as FP64:
  * f_dev[9][ny][nx] and g_dev[5][ny][nx] (device, caller-owned), velocity

@@ -255,8 +255,10 @@ void orc_derive(const orc_physical* ph, orc_lattice* lat) {
     double L = (double)(ph->nx - 1); /* walls on the perimeter nodes */
     double cs = sqrt(CS2);
     double cT2 = (4.0 + ph->varpi) / 10.0;
-    /* Eq. 37 (second occurrence) */
-    double tau_nu = 0.5 + ph->Ma * ph->J * L / cs * sqrt(ph->Pr / ph->Ra);
+    int cooled = ph->thermal_bc == 1;
+    /* Eq. 37 (second occurrence); Section 4.2 writes it with Ra_I */
+    double Rs = cooled ? ph->RaI : ph->Ra;
+    double tau_nu = 0.5 + ph->Ma * ph->J * L / cs * sqrt(ph->Pr / Rs);
     double tau_T = 0.5 + CS2 * (tau_nu - 0.5) / (ph->sigma * cT2 * ph->Pr);
     /* Section 4 rate choices */
     double s[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, 1.0 / tau_nu, 1.0 / tau_nu};
@@ -276,10 +278,15 @@ void orc_derive(const orc_physical* ph, orc_lattice* lat) {
     lat->varpi = ph->varpi;
     lat->Th = ph->Th;
     lat->Tc = ph->Tc;
-    lat->T0 = 0.5 * (ph->Th + ph->Tc);
+    lat->T0 = cooled ? ph->Tc : 0.5 * (ph->Th + ph->Tc);
     lat->L = L;
     lat->dT = dT;
     lat->adiabatic_order = 1;
+    lat->thermal_bc = ph->thermal_bc;
+    /* A9: alpha_e = sigma (4 + varpi)/10 (tau_T - 1/2) */
+    double alpha = ph->sigma * cT2 * (tau_T - 0.5);
+    if (cooled) lat->Q = dT * alpha / (L * L);
+    else if (ph->RaI > 0.0) lat->Q = ph->RaI / ph->Ra * alpha * dT / (L * L);
 }
 
 /* ---- state ----------------------------------------------------------------- */

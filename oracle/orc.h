@@ -47,7 +47,9 @@ typedef struct {
     double phi;            /* mean porosity                                       */
     double Ma;             /* Mach number U / c_s (Section 4)                     */
     double sigma, varpi;   /* thermal capacity ratio, D2Q5 constant (Eq. 29)      */
-    double Th, Tc;         /* wall temperatures                                   */
+    double Th, Tc;         /* wall temperatures (Section 4.2: Th - Tc is the scale dT) */
+    double RaI;            /* internal Rayleigh number, 0 = no heat source        */
+    int thermal_bc;        /* 0: side-heated cavity (Section 4.1, 4.3); 1: every wall at Tc (4.2) */
 } orc_physical;
 
 /* Lattice-level parameters of one run.  Produced by orc_derive() from the
@@ -78,7 +80,11 @@ typedef struct orc_state orc_state;
 
 /* Eq. 37 (second occurrence, Section 4) and the constants of Section 4:
  * rho0 = 1, delta_t = 1, s = (1, 1.1, 1.1, 1, 1.2, 1, 1.2, 1/tau_nu, 1/tau_nu),
- * zeta = (1, 1/tau_T, 1/tau_T, 1.5, 1.5), K = Da L^2, gbeta from U = Ma c_s. */
+ * zeta = (1, 1/tau_T, 1/tau_T, 1.5, 1.5), K = Da L^2, gbeta from U = Ma c_s.
+ * Internal heating: with thermal_bc = 1 (Section 4.2) tau_nu uses Ra_I in
+ * place of Ra, T0 = Tc and dT = Q''' L^2 / alpha_e; with thermal_bc = 0 and
+ * RaI > 0 (Section 4.3) Q''' follows from Ra_I / Ra = Q''' L^2 / (alpha_e dT)
+ * (definitions of Section 2), alpha_e from A9. */
 void orc_derive(const orc_physical* ph, orc_lattice* lat);
 
 /* Creates a run.  phi_field (ny*nx, optional) gives a per-cell porosity; K and

@@ -42,7 +42,8 @@ class Physical(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int),
                 ("Ra", C.c_double), ("Da", C.c_double), ("Pr", C.c_double), ("J", C.c_double),
                 ("phi", C.c_double), ("Ma", C.c_double), ("sigma", C.c_double),
-                ("varpi", C.c_double), ("Th", C.c_double), ("Tc", C.c_double)]
+                ("varpi", C.c_double), ("Th", C.c_double), ("Tc", C.c_double),
+                ("RaI", C.c_double), ("thermal_bc", C.c_int)]
 
 
 class Lattice(C.Structure):
@@ -99,9 +100,9 @@ def lib():
 
 
 def derive(nx, ny, Ra, Da, phi, Pr=1.0, J=1.0, Ma=0.1, sigma=1.0, varpi=-2.0,
-           Th=1.0, Tc=0.0) -> Lattice:
-    """Lattice parameters of a side-heated cavity (Eq. 37 second occurrence, Section 4)."""
-    ph = Physical(nx, ny, Ra, Da, Pr, J, phi, Ma, sigma, varpi, Th, Tc)
+           Th=1.0, Tc=0.0, RaI=0.0, thermal_bc=0) -> Lattice:
+    """Lattice parameters of a cavity (Eq. 37 second occurrence, Section 4)."""
+    ph = Physical(nx, ny, Ra, Da, Pr, J, phi, Ma, sigma, varpi, Th, Tc, RaI, thermal_bc)
     lat = Lattice()
     lib().orc_derive(C.byref(ph), C.byref(lat))
     return lat

@@ -24,7 +24,8 @@ class Params(C.Structure):
                 ("Th", C.c_double), ("Tc", C.c_double), ("Qppp", C.c_double),
                 ("precision", C.c_int), ("use_phi_field", C.c_int), ("forchheimer", C.c_int),
                 ("thermal_bc", C.c_int), ("adiabatic_order", C.c_int), ("collision", C.c_int),
-                ("block_x", C.c_int), ("block_y", C.c_int), ("nodes_per_thread", C.c_int)]
+                ("block_x", C.c_int), ("block_y", C.c_int), ("nodes_per_thread", C.c_int),
+                ("RaI", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -51,6 +52,10 @@ SIGNATURES = [
     ("lbm_tune", C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lbm_observables", C.c_int, [C.c_void_p, C.POINTER(Obs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_adjoint_step", C.c_int, [C.c_void_p, C.c_long, C.c_long, C.POINTER(C.c_double), C.c_void_p]),
+    ("lbm_run_steady", C.c_int, [C.c_void_p, C.c_double, C.c_long, C.c_long, C.POINTER(C.c_long),
+                                 C.POINTER(C.c_double)]),
+    ("lbm_field_extrema", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     ("lbm_nusselt", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lbm_read_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_checkpoint_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
@@ -40,6 +41,10 @@ struct lbm_handle_s {
     double* obs_host = nullptr;
     int* status_dev = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t steady_exec = nullptr;
+    long steady_key[4] = {0, 0, 0, 0};  // K, parity, max_checks, tol bits
+    double* steady_dev = nullptr;       // 8 doubles of loop state
+    double* extrema_dev = nullptr;      // 3 doubles per column
     int bx = 128, by = 2, npt = 1;
     std::string err;
 };
@@ -68,11 +73,14 @@ int cuda_fail(lbm_handle h, cudaError_t e, const char* where) {
 int derive(const lbm_params* p, Derived* dv, std::string* why) {
     if (p->nx < 5 || p->ny < 5) return *why = "nx and ny must be >= 5", LBM_ERR_ARG;
     if (!(p->phi > 0.0 && p->phi <= 1.0)) return *why = "phi must lie in (0, 1]", LBM_ERR_ARG;
-    if (!(p->Ra > 0.0) || !(p->Da > 0.0) || !(p->Pr > 0.0) || !(p->J > 0.0) || !(p->Ma > 0.0))
-        return *why = "Ra, Da, Pr, J and Ma must be positive", LBM_ERR_ARG;
+    const bool cooled = p->thermal_bc == LBM_BC_COOLED;
+    if (!(p->Da > 0.0) || !(p->Pr > 0.0) || !(p->J > 0.0) || !(p->Ma > 0.0) || !(p->RaI >= 0.0))
+        return *why = "Da, Pr, J and Ma must be positive and RaI non-negative", LBM_ERR_ARG;
+    if (cooled ? !(p->RaI > 0.0) : !(p->Ra > 0.0))
+        return *why = "Ra must be positive (RaI for LBM_BC_COOLED)", LBM_ERR_ARG;
     if (!(p->sigma > 0.0) || !(p->varpi < 1.0) || !(p->varpi > -4.0))
         return *why = "sigma must be positive and varpi in (-4, 1)", LBM_ERR_ARG;
-    if (!(p->Th > p->Tc)) return *why = "Th must exceed Tc", LBM_ERR_ARG;
+    if (!(p->Th > p->Tc)) return *why = "Th must exceed Tc (with LBM_BC_COOLED, Th - Tc is the scale dT)", LBM_ERR_ARG;
     if (p->precision < LBM_F64 || p->precision > LBM_F32_STORE_F16) return *why = "bad precision", LBM_ERR_ARG;
     if (p->use_phi_field && !(p->phi < 1.0))
         return *why = "a porosity field needs a mean porosity below 1", LBM_ERR_ARG;
@@ -84,7 +92,9 @@ int derive(const lbm_params* p, Derived* dv, std::string* why) {
     const double L = (double)(p->nx - 1);
     const double cT2 = (4.0 + p->varpi) / 10.0;
     dv->L = L;
-    dv->tau_nu = 0.5 + p->Ma * p->J * L / cs * sqrt(p->Pr / p->Ra);
+    // Eq. 37 (second occurrence); Section 4.2 replaces Ra by Ra_I when Ra = 0
+    const double Rs = cooled ? p->RaI : p->Ra;
+    dv->tau_nu = 0.5 + p->Ma * p->J * L / cs * sqrt(p->Pr / Rs);
     dv->tau_T = 0.5 + cs2 * (dv->tau_nu - 0.5) / (p->sigma * cT2 * p->Pr);
     if (!(dv->tau_nu > 0.5) || !(dv->tau_T > 0.5)) return *why = "relaxation time not above 1/2", LBM_ERR_ARG;
     dv->nu = cs2 * (dv->tau_nu - 0.5) / p->J;
@@ -93,7 +103,13 @@ int derive(const lbm_params* p, Derived* dv, std::string* why) {
     dv->gbeta = U * U / (dv->dT * L);
     dv->K = p->Da * L * L;
     dv->Fphi = p->forchheimer ? 1.75 / sqrt(150.0 * p->phi * p->phi * p->phi) : 0.0;
-    dv->T0 = 0.5 * (p->Th + p->Tc);
+    // buoyancy reference: the mean wall temperature (Section 4.1), T_c with internal heating only (Section 4.2)
+    dv->T0 = cooled ? p->Tc : 0.5 * (p->Th + p->Tc);
+    // heat source: Ra_I / Ra = Q L^2 / (alpha_e dT) (Section 2), alpha_e from A9
+    const double alpha = p->sigma * cT2 * (dv->tau_T - 0.5);
+    if (cooled) dv->Q = dv->dT * alpha / (L * L);
+    else if (p->RaI > 0.0) dv->Q = p->RaI / p->Ra * alpha * dv->dT / (L * L);
+    else dv->Q = p->Qppp;
     return LBM_OK;
 }
 
@@ -126,11 +142,11 @@ void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
     c->inv_csT2 = (R)(10.0 / (4.0 + p->varpi));
     c->wt0 = (R)((1.0 - p->varpi) / 5.0);
     c->wt1 = (R)((4.0 + p->varpi) / 20.0);
-    c->psi0 = (R)(p->Qppp / p->sigma);
-    c->psi3 = (R)(p->varpi * p->Qppp / p->sigma);
-    c->qhalf = (R)(0.5 * p->Qppp / p->sigma);
+    c->psi0 = (R)(dv.Q / p->sigma);
+    c->psi3 = (R)(p->varpi * dv.Q / p->sigma);
+    c->qhalf = (R)(0.5 * dv.Q / p->sigma);
     c->phi = (R)p->phi;
-    c->c_lin = (R)(p->phi * dv.nu / dv.K);
+    c->c_lin = (R)(p->phi * dv.nu / dv.K);  // 0 when Da = INFINITY
     c->c_quad = (R)(p->phi * dv.Fphi / sqrt(dv.K));
     // per-cell Ergun (Eq. 5) with d_p^2 fixed by K(phi_bar) = K_bar:
     // phi nu / K(phi) = 150 nu (1-phi)^2 / (phi^2 d_p^2), phi F_phi / sqrt K = 1.75 (1-phi) / (phi^2 d_p)
@@ -179,6 +195,9 @@ void free_handle(lbm_handle h) {
         if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
         if (h->buf[k]) cudaFree(h->buf[k]);
     }
+    if (h->steady_exec) cudaGraphExecDestroy(h->steady_exec);
+    if (h->steady_dev) cudaFree(h->steady_dev);
+    if (h->extrema_dev) cudaFree(h->extrema_dev);
     if (h->phi) cudaFree(h->phi);
     if (h->snap) cudaFree(h->snap);
     if (h->partials) cudaFree(h->partials);
@@ -246,6 +265,60 @@ void drop_graphs(lbm_handle h) {
             cudaGraphExecDestroy(h->gexec[k]);
             h->gexec[k] = nullptr;
         }
+    if (h->steady_exec) {
+        cudaGraphExecDestroy(h->steady_exec);
+        h->steady_exec = nullptr;
+    }
+}
+
+// The steady-state graph: while (cond) { K steps; check }.
+int build_steady_graph(lbm_handle h, long K, long max_checks, double tol) {
+    cudaGraph_t g = nullptr;
+    CK(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            int src = h->cur;
+            for (long k = 0; k < K && e == cudaSuccess; ++k) {
+                e = launch_step(step_launch(h, src, h->cap_stream), h->coef);
+                src ^= 1;
+            }
+            if (e == cudaSuccess) {
+                SteadyCheckLaunch L;
+                L.precision = h->precision;
+                L.prev = h->buf[h->cur ^ 1];
+                L.gm = h->gm;
+                L.L = h->dv.L;
+                L.dT = h->dv.dT;
+                L.status = h->status_dev;
+                L.tol = tol;
+                L.max_checks = max_checks;
+                L.state = h->steady_dev;
+                L.cond = cond;
+                L.stream = h->cap_stream;
+                e = launch_steady_check(L, h->coef);
+            }
+            cudaGraph_t out = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->steady_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "steady-state graph");
+    return LBM_OK;
 }
 
 }  // namespace
@@ -603,6 +676,56 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
     }
     release();
     return rc;
+}
+
+int lbm_run_steady(lbm_handle h, double tol, long check_every, long max_steps, long* steps_taken, double* change) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!(tol > 0.0) || check_every < 1 || max_steps < 1) return fail(h, LBM_ERR_ARG, "need tol > 0, check_every >= 1, max_steps >= 1");
+    const long K = (check_every + 1) / 2 * 2;  // even: the captured buffers return to their parity
+    const long max_checks = (max_steps + K - 1) / K;
+    if (!h->steady_dev) CK(h, cudaMalloc(&h->steady_dev, 8 * sizeof(double)));
+    long tolbits;
+    memcpy(&tolbits, &tol, sizeof tolbits);
+    const long key[4] = {K, h->cur, max_checks, tolbits};
+    if (!h->steady_exec || memcmp(key, h->steady_key, sizeof key) != 0) {
+        if (h->steady_exec) cudaGraphExecDestroy(h->steady_exec);
+        h->steady_exec = nullptr;
+        int rc = build_steady_graph(h, K, max_checks, tol);
+        if (rc != LBM_OK) return rc;
+        memcpy(h->steady_key, key, sizeof key);
+    }
+    CK(h, cudaMemsetAsync(h->steady_dev, 0, 8 * sizeof(double), h->stream));
+    CK(h, cudaGraphLaunch(h->steady_exec, h->stream));
+    double st[8];
+    CK(h, cudaMemcpyAsync(st, h->steady_dev, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const long steps = (long)st[3] * K;
+    h->t += steps;
+    h->snap_valid = 0;
+    if (steps_taken) *steps_taken = steps;
+    if (change) *change = st[2];
+    if ((int)st[4] == 2) return fail(h, LBM_ERR_DIVERGED, "divergence flag raised during the steady-state loop");
+    return LBM_OK;
+}
+
+int lbm_field_extrema(lbm_handle h, double* T_max, double* psi_min, double* psi_max) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->extrema_dev) CK(h, cudaMalloc(&h->extrema_dev, 3 * sizeof(double) * (size_t)h->p.nx));
+    CK(h, launch_extrema(h->precision, h->buf[h->cur ^ 1], h->p.use_phi_field ? h->phi : nullptr, h->gm, h->coef,
+                         h->extrema_dev, h->stream));
+    std::vector<double> col(3 * (size_t)h->p.nx);
+    CK(h, cudaMemcpyAsync(col.data(), h->extrema_dev, sizeof(double) * col.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double tm = -INFINITY, pmn = 0.0, pmx = 0.0;
+    for (int x = 0; x < h->p.nx; ++x) {
+        tm = fmax(tm, col[3 * x]);
+        pmn = fmin(pmn, col[3 * x + 1]);
+        pmx = fmax(pmx, col[3 * x + 2]);
+    }
+    if (T_max) *T_max = tm;
+    if (psi_min) *psi_min = pmn;
+    if (psi_max) *psi_max = pmx;
+    return LBM_OK;
 }
 
 int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev) {

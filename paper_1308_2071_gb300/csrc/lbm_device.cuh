@@ -500,4 +500,60 @@ __device__ __forceinline__ typename T::R node_dT(const Coef<typename T::R>& c, c
     return dTf;
 }
 
+// Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).
+__device__ __forceinline__ void block_reduce4(double v[4], double* sh /* 4 * 32 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[k * 32 + warp] = v[k];
+    }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (lane < nw) ? sh[k * 32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+            v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+            v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+            v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+        }
+    }
+}
+
+// Mean Nusselt numbers (Eq. 38) of both vertical walls over the whole block
+// (valid in thread 0): Nu(y) = -L dT/dx / dT with the one-sided five-point
+// derivative (-25 T0 + 48 T1 - 36 T2 + 16 T3 - 3 T4) / 12, trapezoidal mean
+// over y, FP64.  sh: 4 * 32 doubles of shared memory.
+template <class T>
+__device__ __forceinline__ void nusselt_block(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& prev,
+                                              double L, double dT, double* sh, double* nu_hot, double* nu_cold) {
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    const int nx = gm.nx;
+    for (int y = threadIdx.x; y < gm.ny; y += blockDim.x) {
+        double tl[5], tr[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
+            tr[k] = (double)node_dT<T>(c, gm, prev, nx - 1 - k, y);
+        }
+        const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
+        const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
+        const double wt = (y == 0 || y == gm.ny - 1) ? 0.5 : 1.0;
+        w[2] += wt * (-L * dl / dT);
+        w[3] += wt * (-L * dr / dT);
+    }
+    block_reduce4(w, sh);
+    *nu_hot = w[2] / (double)(gm.ny - 1);
+    *nu_cold = w[3] / (double)(gm.ny - 1);
+}
+
 }  // namespace lbm

@@ -14,7 +14,7 @@ namespace lbm {
 
 // Lattice parameters derived from lbm_params (Section 4 set-up).
 struct Derived {
-    double L, tau_nu, tau_T, nu, gbeta, K, Fphi, T0, dT;
+    double L, tau_nu, tau_T, nu, gbeta, K, Fphi, T0, dT, Q;
 };
 
 // Validates p and fills the derived parameters, the coefficients in both
@@ -106,6 +106,23 @@ struct AdjointJob {
     cudaStream_t stream;
 };
 cudaError_t launch_adjoint_sweep(const AdjointJob& J);
+
+struct SteadyCheckLaunch {
+    int precision;
+    const void* prev;
+    Geom gm;
+    double L, dT;
+    const int* status;
+    double tol;
+    long max_checks;
+    double* state;  // 8 doubles
+    cudaGraphConditionalHandle cond;
+    cudaStream_t stream;
+};
+cudaError_t launch_steady_check(const SteadyCheckLaunch& L, const CoefSet& cs);
+// out: 3 doubles per column (max T, min psi, max psi)
+cudaError_t launch_extrema(int precision, const void* prev, const void* phi, const Geom& gm, const CoefSet& cs,
+                           double* out, cudaStream_t s);
 
 // Bytes of one state buffer (9 flow + 5 thermal planes) and of a porosity field.
 size_t state_buffer_bytes(int precision, int plane);

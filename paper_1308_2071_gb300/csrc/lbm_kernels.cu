@@ -38,35 +38,6 @@ __global__ void __launch_bounds__(256) k_step2(Src<T> src, Dst<T> dst, const typ
 
 // ---- observables ------------------------------------------------------------------
 
-// Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).
-__device__ __forceinline__ void block_reduce4(double v[4], double* sh /* 4 * 32 */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
-        v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
-        v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sh[k * 32 + warp] = v[k];
-    }
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (lane < nw) ? sh[k * 32 + lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-            v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
-            v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
-            v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
-        }
-    }
-}
-
 // Macroscopic fields of the post-stream state S_n, rebuilt by pulling from
 // B_{n-1} and applying the wall rule, plus per-block partials (FP64) of
 // max|u|, max|u - u_prev|, sum of population deviations, sum of T - T0.
@@ -135,25 +106,11 @@ __global__ void __launch_bounds__(1024) k_finish(Src<T> prev, Geom gm, Coef<type
     block_reduce4(v, sh);
     __syncthreads();
     const double red[4] = {v[0], v[1], v[2], v[3]};
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    const int nx = gm.nx;
-    for (int y = threadIdx.x; y < gm.ny; y += blockDim.x) {
-        double tl[5], tr[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
-            tr[k] = (double)node_dT<T>(c, gm, prev, nx - 1 - k, y);
-        }
-        const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
-        const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
-        const double wt = (y == 0 || y == gm.ny - 1) ? 0.5 : 1.0;
-        w[2] += wt * (-L * dl / dT);
-        w[3] += wt * (-L * dr / dT);
-    }
-    block_reduce4(w, sh);
+    double nh, nc;
+    nusselt_block<T>(c, gm, prev, L, dT, sh, &nh, &nc);
     if (threadIdx.x == 0) {
-        out[0] = w[2] / (double)(gm.ny - 1);
-        out[1] = w[3] / (double)(gm.ny - 1);
+        out[0] = nh;
+        out[1] = nc;
         out[2] = red[0];
         out[3] = red[1];
         out[4] = red[2];

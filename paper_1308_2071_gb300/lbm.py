@@ -129,6 +129,20 @@ class Cavity:
                                           C.c_void_p(out.data_ptr())), self._h)
         return J.value, out
 
+    def run_steady(self, tol: float = 1e-9, check_every: int = 1000, max_steps: int = 10_000_000):
+        """Steps until both wall Nusselt numbers change by less than tol
+        (relative) between checks, on the device; returns (steps, change)."""
+        n, ch = C.c_long(), C.c_double()
+        L.check(L.load().lbm_run_steady(self._h, float(tol), int(check_every), int(max_steps), C.byref(n),
+                                        C.byref(ch)), self._h)
+        return n.value, ch.value
+
+    def extrema(self):
+        """(T max, psi min, psi max) of the current state, lattice units."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        L.check(L.load().lbm_field_extrema(self._h, C.byref(a), C.byref(b), C.byref(c)), self._h)
+        return a.value, b.value, c.value
+
     def nusselt(self):
         """(Nu of the hot wall, Nu of the cold wall), FP64 (Eq. 38)."""
         a, b = C.c_double(), C.c_double()

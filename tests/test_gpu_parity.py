@@ -184,6 +184,53 @@ def test_porosity_field_matches_oracle(precision, tol, nthreads):
     assert max(eu, eT, en) < tol, (eu, eT, ep, en)
 
 
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f32", 2e-4), ("f16", 2e-3)])
+def test_lognormal_porosity_field_matches_oracle(precision, tol, nthreads):
+    # the heterogeneous input of the 8192^2 workload, at 128^2 (correlation length 8)
+    import torch
+
+    from paper_1308_2071_gb300.inputs import porosity_field
+
+    n = 128
+    phi = porosity_field(n, n, phi_bar=0.6, corr_len=8.0, seed=1308)
+    assert 0.3 <= phi.min() and phi.max() <= 0.9 and phi.std() > 0.05
+    lat = derive(n, n, Ra=1e5, Da=1e-4, phi=0.6)
+    o = Oracle(lat, phi_field=phi).step(600, threads=nthreads)
+    cav = cavity(n, n, Ra=1e5, Da=1e-4, phi=0.6, precision=precision, phi_field=torch.from_numpy(phi).cuda())
+    cav.step(600)
+    eu, eT, ep, en = field_errors(cav.observables(fields=True), o)
+    assert max(eu, eT, en) < tol, (eu, eT, ep, en)
+
+
+def test_max_size_one_step_with_porosity_field(nthreads):
+    # 8192^2 with the seeded log-normal field, FP32, two nodes per thread: every
+    # population after one step from the GPU's own state, against the oracle.
+    import torch
+
+    from paper_1308_2071_gb300.inputs import porosity_field
+
+    n = 8192
+    phi = porosity_field(n, n, phi_bar=0.6, corr_len=32.0, seed=1308)
+    cav = cavity(n, n, Ra=1e5, Da=1e-4, phi=0.6, precision="f32", phi_field=torch.from_numpy(phi).cuda(),
+                 nodes_per_thread=2)
+    cav.step(40)
+    f, g = cav.read_state()
+    fh, gh = np_(f), np_(g)
+    del f, g
+    o = Oracle(derive(n, n, Ra=1e5, Da=1e-4, phi=0.6), phi_field=phi)
+    o.set_state(fh, gh)
+    del fh, gh
+    o.step(1, threads=nthreads)
+    cav.step(1)
+    f1, g1 = cav.read_state()
+    fo, go = o.state()
+    for q in range(9):
+        assert np.abs(np_(f1[q]) - fo[q]).max() < 2e-7, q
+    for q in range(5):
+        assert np.abs(np_(g1[q]) - go[q]).max() < 2e-7, q
+    cav.close()
+
+
 # ---- full size, bench launch configuration ----------------------------------------
 
 def test_full_size_one_step_fp32(nthreads):
@@ -287,3 +334,37 @@ def test_step_autotuner_resets_and_caches(tmp_path):
     cav.step(40)
     cav2.step(40)
     assert np.array_equal(np_(cav.read_state()[0]), np_(cav2.read_state()[0]))
+
+
+# ---- internal heat generation (Sections 4.2-4.3) and Da = infinity ------------------
+
+@pytest.mark.parametrize("case", ["cooled", "side_heated", "no_darcy"])
+def test_internal_heating_and_infinite_darcy_match_oracle(case, nthreads):
+    n = 48
+    if case == "cooled":  # Section 4.2 set-up: every wall at Tc, Ra = 0, Brinkman model
+        kw = dict(Ra=0.0, Da=1e-2, phi=1.0, Pr=7.0, RaI=6.4e5, thermal_bc=1)
+        lat = derive(n, n, Ra=0.0, Da=1e-2, phi=1.0, Pr=7.0, RaI=6.4e5, thermal_bc=1)
+        lat.forchheimer = 0
+        extra = dict(forchheimer=0)
+    elif case == "side_heated":  # Section 4.3 set-up
+        kw = dict(Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e7)
+        lat = derive(n, n, Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e7)
+        extra = {}
+    else:  # pure fluid limit with no Darcy drag
+        kw = dict(Ra=1e5, Da=float("inf"), phi=1.0, Pr=0.71)
+        lat = derive(n, n, Ra=1e5, Da=float("inf"), phi=1.0, Pr=0.71)
+        lat.forchheimer = 0
+        extra = dict(forchheimer=0)
+    o = Oracle(lat).step(700, threads=nthreads)
+    cav = cavity(n, n, precision="f64", **kw, **extra)
+    cav.step(700)
+    obs = cav.observables(fields=True)
+    eu, eT, ep, en = field_errors(obs, o)
+    if case == "cooled":
+        # internal heating has barely set the fluid moving after 700 steps:
+        # measure the velocity error against the velocity scale U = Ma c_s
+        oux, ouy, _, _ = o.macros()
+        U = 0.1 / np.sqrt(3.0)
+        eu = max(np.abs(np_(obs["ux"]) - oux).max(), np.abs(np_(obs["uy"]) - ouy).max()) / U
+    assert max(eu, eT, ep) < 1e-11, (eu, eT, ep, en)
+    assert en < 1e-10 or case == "cooled", en

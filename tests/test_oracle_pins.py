@@ -421,3 +421,53 @@ def test_table2_proximity_coarse_grid(nthreads):
         prev = nl
     nu = 0.5 * (nl + nr)
     assert abs(nu / row[3] - 1) < 0.015, (nl, nr, row[3])
+
+
+def _source_conduction_error(n, tau_T):
+    lat = derive(n, 5, Ra=1e4, Da=1e-2, phi=0.6)
+    lat.gbeta = 0.0
+    lat.periodic_y = 1
+    lat.thermal_bc = 1
+    lat.Tc = 0.0
+    lat.T0 = 0.0
+    lat.zeta[1] = lat.zeta[2] = 1.0 / tau_T
+    alpha = 0.2 * (tau_T - 0.5)  # A9 with sigma = 1, varpi = -2
+    L = n - 1
+    lat.Q = 0.1 * alpha / L ** 2
+    o = Oracle(lat).step(int(8 * L * L / alpha), threads=1)
+    T = o.macros()[3][2]
+    x = np.arange(n)
+    exact = lat.Q * x * (L - x) / (2 * alpha)
+    return np.abs(T - exact).max() / exact.max()
+
+
+def test_heat_source_conduction_closed_form():
+    # Eq. 30, 33-36 with a constant source Q and no flow: between two walls at
+    # Tc (periodic in y) the steady temperature is Tc + Q x (L - x) / (2 alpha_e),
+    # alpha_e from A9.  With zeta_1 = 1 the scheme reproduces it exactly; with
+    # zeta_1 != 1 the wall extrapolation leaves a second-order error.
+    assert _source_conduction_error(17, 1.0) < 1e-11
+    assert _source_conduction_error(33, 1.0) < 1e-11
+    e1 = _source_conduction_error(17, 0.75)
+    e2 = _source_conduction_error(33, 0.75)
+    assert e1 < 1e-2 and abs(np.log2(e1 / e2) - 2.0) < 0.05
+
+
+def test_internal_heating_parameters_follow_the_definitions():
+    # Section 4.2: tau_nu from Ra_I, T0 = Tc, dT = Q L^2 / alpha_e;
+    # Section 4.3: Ra_I / Ra = Q L^2 / (alpha_e dT).
+    n = 121
+    L = n - 1
+    lat = derive(n, n, Ra=0.0, Da=1e-2, phi=1.0, Pr=7.0, RaI=6.4e5, thermal_bc=1)
+    nu = (1 / lat.s[7] - 0.5) / 3
+    alpha = 0.2 * (1 / lat.zeta[1] - 0.5)
+    assert abs(nu / alpha / 7.0 - 1) < 1e-12
+    assert lat.T0 == lat.Tc == 0.0 and lat.thermal_bc == 1
+    assert abs(lat.Q * L * L / alpha / lat.dT - 1) < 1e-12
+    RaI = lat.gbeta * lat.Q * L ** 5 / (nu * alpha ** 2)
+    assert abs(RaI / 6.4e5 - 1) < 1e-12
+    lat4 = derive(151, 151, Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e7)
+    nu4 = (1 / lat4.s[7] - 0.5) / 3
+    a4 = 0.2 * (1 / lat4.zeta[1] - 0.5)
+    assert abs(lat4.gbeta * lat4.Q * 150 ** 5 / (nu4 * a4 ** 2) / 1e7 - 1) < 1e-12
+    assert lat4.T0 == 0.5
