@@ -164,14 +164,23 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the slowest replica's time); the tensor lives
+    where the process group's backend wants it (NCCL: GPU, gloo: host)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_mlups(nodes_per_rank, steps, ms_max, world):
+    """Whole-job throughput of N independent replicas: every rank's node
+    updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / (ms_max * 1e-3) / 1e6
 
 
 # ---- legs ----------------------------------------------------------------------------
@@ -411,7 +420,7 @@ def main():
     ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local, shapes=shapes)
     ms = max_over_ranks(ms, world)
     nodes = a.size * a.size
-    mlups = world * nodes * a.steps / (ms * 1e-3) / 1e6
+    mlups = replica_mlups(nodes, a.steps, ms, world)
     peak, peak_kind = load_peaks()
     per_launch_s = ms * 1e-3 / a.steps
     achieved = nodes * BYTES_PER_NODE[a.precision] / per_launch_s / 1e9
