@@ -285,7 +285,8 @@ def batched_leg(steps, warmup, ncav=256, seed=2071):
     gbs = nodes * BYTES_PER_NODE["f32"] / (ms * 1e-3 / steps) / 1e9
     return dict(cavities=ncav, nodes=nodes, steps=steps, mlups=round(nodes * steps / (ms * 1e-3) / 1e6, 2),
                 hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / peak, 4), tile=[tw, th], blocks_per_sm=bps,
-                nodes_per_thread=tw * th // 256, mode="one persistent cooperative launch per call, graph-captured",
+                nodes_per_thread=1 if tw * th in (32, 256) else 2,
+                mode="one persistent cooperative launch per call, graph-captured",
                 blocks=q["nblocks"], tiles=q["ntiles"], launches=1, diverged=int(st.sum()),
                 status=int(rc), sizes="U{64..512} square, seed %d" % seed)
 

@@ -245,9 +245,9 @@ int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold);
 int lbm_batch_status(lbm_batch b, int* status);
 /* FP64 post-stream populations of cavity cav (as lbm_read_state). */
 int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev);
-/* Upper bound on the polls (about 0.1 us or more each) a block spends at the
- * grid barrier before it records LBM_ERR_TIMEOUT and leaves the kernel;
- * default 2e7.  Also clears a previous timeout. */
+/* Upper bound on the polls (sleeps of 32 ns growing to 1 us between them) a
+ * block spends at the grid barrier before it records LBM_ERR_TIMEOUT and
+ * leaves the kernel; default 2e7.  Also clears a previous timeout. */
 int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
 /* Autotuner: times candidate tile shapes (tile_w x tile_h nodes), blocks per
  * SM and the two scheduling modes on this batch, keeps the fastest, and records it in a text cache
@@ -255,11 +255,15 @@ int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
  * cache); a cached entry is reused without timing.  Tuning advances the
  * lattices, so the batch is reset to t = 0 afterwards.  Outputs may be NULL. */
 int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm);
-/* Sets the tile shape (tile_w a power of two, tile_w x tile_h = 256 nodes: one
- * node per thread, or 512: two), blocks per SM (0 = as many as fit) and the
- * scheduling (dynamic = 0: each block owns a contiguous run of tiles;
- * 1: blocks take chunks of 4 tiles from a per-step counter) without timing;
- * resets the batch to t = 0. */
+/* Sets the tile shape (tile_w a power of two >= 32; tile_w x tile_h = 256 or
+ * 512 nodes run on 256-thread blocks, 32 or 64 nodes on one-warp blocks; the
+ * larger size of each pair is two nodes per thread), blocks per SM (0 = as
+ * many as fit) and the scheduling without timing: dynamic = 0, each block
+ * owns a contiguous run of tiles and a grid barrier ends every step; 1, blocks
+ * take chunks of 4 tiles from a per-step counter, same barrier; 2, dataflow:
+ * blocks take (step, tile) items in order from one counter and an item of
+ * step s waits (bounded, like the barrier) only for its own cavity's step
+ * s - 1, so no grid-wide barrier.  Resets the batch to t = 0. */
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic);
 /* Steps taken, number of tiles and blocks of the persistent launch. */
 int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks);

@@ -24,6 +24,7 @@ namespace lbm {
 template <class R> struct CavDesc {
     Geom gm;
     void* buf[2];  // B_n / B_{n+1} ping-pong of this cavity
+    int ntiles;    // tiles covering this cavity
     Coef<R> c;
 };
 
@@ -33,7 +34,7 @@ struct Tile {
 
 // Bounded sense-reversing grid barrier.  Thread 0 of each block arrives on
 // count; the last arrival resets count and bumps gen; the others wait for gen
-// to change, at most `limit` polls of ~0.1-1 us each.  Returns false (in every
+// to change, at most `limit` polls (sleeps growing from 32 ns to 1 us).  Returns false (in every
 // thread of the block) when the wait ran out.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
                                              long long limit, int* flag, int* reset_on_release) {
@@ -51,13 +52,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
             atomicAdd((unsigned*)gen, 1u);
         } else {
             long long polls = 0;
+            unsigned ns = 32;  // exponential back-off keeps thousands of pollers off the L2 slice
             while (*gen == g) {
                 if (++polls > limit) {
                     ok = 0;
                     atomicOr(flag, 1);
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(ns);
+                ns = ns < 1024 ? 2 * ns : 1024;
             }
         }
         __threadfence();
@@ -84,6 +87,106 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
     // cavity); dynamic mode: blocks take chunks of kChunk tiles from a per-step
     // counter.  Either way the block restages the descriptor only when the
     // cavity changes.
+    if (dyn == 2) {
+        // dataflow: work items (step, tile) in step-major order from one
+        // counter; an item of step s > 0 waits until its cavity has finished
+        // step s - 1 (every tile of it was taken earlier by a resident block).
+        __shared__ unsigned long long base_sh;
+        __shared__ int ok_sh;
+        const unsigned long long total = (unsigned long long)nsteps * (unsigned long long)ntiles;
+        int cur_cav = -1;
+        int ok_cav = -1;        // (cavity, step) whose dependency this block last verified
+        long ok_step = -1;
+        int pend_cav = -1;      // finished tiles not yet published (thread 0's view)
+        int pend_n = 0;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) base_sh = atomicAdd((unsigned long long*)tile_ctr, (unsigned long long)kChunk);
+            __syncthreads();
+            const unsigned long long base = base_sh;
+            if (base >= total) break;
+            const unsigned long long end = base + kChunk < total ? base + kChunk : total;
+            for (unsigned long long it = base; it < end; ++it) {
+                const long sstep = (long)(it / (unsigned long long)ntiles);
+                const int t = (int)(it - (unsigned long long)sstep * (unsigned long long)ntiles);
+                const Tile tl = tiles[t];
+                if (threadIdx.x == 0 && pend_n > 0 && pend_cav != tl.cav) {
+                    // publish before waiting on anything else (keeps the progress argument)
+                    __threadfence();
+                    atomicAdd((int*)&bar_count[2 + pend_cav], pend_n);
+                    pend_n = 0;
+                }
+                if (sstep > 0 && !(tl.cav == ok_cav && sstep == ok_step)) {
+                    if (threadIdx.x == 0) {
+                        if (pend_n > 0) {
+                            __threadfence();
+                            atomicAdd((int*)&bar_count[2 + pend_cav], pend_n);
+                            pend_n = 0;
+                        }
+                        const int need = (int)sstep * cavs[tl.cav].ntiles;
+                        volatile int* dn = (volatile int*)&bar_count[2 + tl.cav];
+                        long long polls = 0;
+                        unsigned ns = 32;
+                        int ok = 1;
+                        while (*dn < need) {
+                            if (++polls > wait_limit) {
+                                ok = 0;
+                                atomicOr(timeout_flag, 1);
+                                break;
+                            }
+                            __nanosleep(ns);
+                            ns = ns < 1024 ? 2 * ns : 1024;
+                        }
+                        __threadfence();
+                        ok_sh = ok;
+                    }
+                    __syncthreads();
+                    if (!ok_sh) return;
+                    ok_cav = tl.cav;
+                    ok_step = sstep;
+                }
+                if (tl.cav != cur_cav) {
+                    __syncthreads();
+                    const int* srcw = (const int*)&cavs[tl.cav];
+                    int* dstw = (int*)&cd;
+                    for (int k = threadIdx.x; k < (int)(sizeof(CavDesc<R>) / sizeof(int)); k += blockDim.x)
+                        dstw[k] = srcw[k];
+                    __syncthreads();
+                    cur_cav = tl.cav;
+                }
+                const int ps = (par + (int)(sstep & 1)) & 1;
+                const Geom gm = cd.gm;
+                const Src<T> src = src_view<T>(cd.buf[ps], gm.plane);
+                const Dst<T> dst = dst_view<T>(cd.buf[ps ^ 1], gm.plane);
+                const int msk = (1 << lg_tw) - 1;
+                if constexpr (NPT == 2) {
+                    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+                    const int x0 = tl.x0 + (k0 & msk), y0 = tl.y0 + (k0 >> lg_tw);
+                    const int x1 = tl.x0 + (k1 & msk), y1 = tl.y0 + (k1 >> lg_tw);
+                    update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
+                                          x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
+                } else {
+                    const int x = tl.x0 + (threadIdx.x & msk), y = tl.y0 + (threadIdx.x >> lg_tw);
+                    if (x < gm.nx && y < gm.ny)
+                        update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
+                }
+                // the block's stores happen before this barrier; thread 0's GPU-scope
+                // fence (cumulative) orders them before the count is published
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    if (pend_cav != tl.cav) pend_n = 0;
+                    pend_cav = tl.cav;
+                    ++pend_n;
+                }
+            }
+            if (threadIdx.x == 0 && pend_n > 0) {  // publish at the end of every chunk
+                __threadfence();
+                atomicAdd((int*)&bar_count[2 + pend_cav], pend_n);
+                pend_n = 0;
+            }
+        }
+        return;
+    }
     const int per = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
     for (long s = 0; s < nsteps; ++s) {
         int cur_cav = -1;
@@ -111,10 +214,10 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
                 const Geom gm = cd.gm;
                 const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
                 const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
-                // tiles hold 256 * NPT nodes, tile width 2^lg_tw
+                // tiles hold blockDim.x * NPT nodes, tile width 2^lg_tw
                 const int msk = (1 << lg_tw) - 1;
                 if constexpr (NPT == 2) {
-                    const int k0 = threadIdx.x, k1 = threadIdx.x + 256;
+                    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
                     const int x0 = tl.x0 + (k0 & msk), y0 = tl.y0 + (k0 >> lg_tw);
                     const int x1 = tl.x0 + (k1 & msk), y1 = tl.y0 + (k1 >> lg_tw);
                     update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
@@ -195,6 +298,10 @@ struct TuneChoice {
     int tw = 128, th = 2, blocks_per_sm = 0, dyn = 0;
 };
 
+// Tiles of 256 or 512 nodes run with 256-thread blocks; tiles of 32 or 64
+// nodes with one-warp blocks, whose block synchronisation is a warp's.
+int block_of(const TuneChoice& t) { return t.tw * t.th >= 256 ? 256 : 32; }
+
 }  // namespace
 
 struct lbm_batch_s {
@@ -205,6 +312,7 @@ struct lbm_batch_s {
     std::vector<Geom> gm;
     std::vector<CoefSet> coef;
     std::vector<size_t> off[2];
+    std::vector<int> cav_tiles;
     size_t pool_bytes = 0;
     void* pool = nullptr;
     void* descs = nullptr;  // CavDesc<R>[ncav]
@@ -214,8 +322,8 @@ struct lbm_batch_s {
     double* nu_dev = nullptr;
     int* status = nullptr;  // per cavity
     int* timeout_flag = nullptr;
-    unsigned* bar = nullptr;  // count, gen
-    int* tile_ctr = nullptr;  // dynamic scheduling: one counter per step parity
+    unsigned* bar = nullptr;  // count, gen, then one finished-tile counter per cavity
+    int* tile_ctr = nullptr;  // dynamic: one counter per step parity; dataflow: one 64-bit item counter
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int par = 0;  // parity holding B_n
@@ -249,7 +357,7 @@ template <class T> const void* kernel_ptr(int npt) {
     return npt == 2 ? (const void*)&k_batch<T, 2> : (const void*)&k_batch<T, 1>;
 }
 
-int npt_of(const TuneChoice& t) { return t.tw * t.th == 512 ? 2 : 1; }
+int npt_of(const TuneChoice& t) { return t.tw * t.th == 2 * block_of(t) ? 2 : 1; }
 
 int log2i(int v) {
     int l = 0;
@@ -257,17 +365,24 @@ int log2i(int v) {
     return l;
 }
 
+template <class R> int upload_descs(lbm_batch b);
+
 int build_tiles(lbm_batch b) {
     if (b->stream) BCK(b, cudaStreamSynchronize(b->stream));  // queued launches may still read the old list
     std::vector<Tile> tl;
+    b->cav_tiles.assign(b->ncav, 0);
     for (int c = 0; c < b->ncav; ++c)
         for (int y0 = 0; y0 < b->gm[c].ny; y0 += b->tune.th)
-            for (int x0 = 0; x0 < b->gm[c].nx; x0 += b->tune.tw) tl.push_back(Tile{c, x0, y0});
+            for (int x0 = 0; x0 < b->gm[c].nx; x0 += b->tune.tw) {
+                tl.push_back(Tile{c, x0, y0});
+                ++b->cav_tiles[c];
+            }
     if (b->tiles) cudaFree(b->tiles);
     b->tiles = nullptr;
     b->ntiles = (int)tl.size();
     BCK(b, cudaMalloc(&b->tiles, sizeof(Tile) * tl.size()));
     BCK(b, cudaMemcpy(b->tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice));
+    if (b->descs) return b->precision == LBM_F64 ? upload_descs<double>(b) : upload_descs<float>(b);
     return LBM_OK;
 }
 
@@ -276,7 +391,7 @@ int grid_size(lbm_batch b, int* nblocks) {
     BCK(b, cudaGetDevice(&dev));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt_of(b->tune)) : kernel_ptr<PrecF32P>(npt_of(b->tune));
-    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_of(b->tune), 0));
     if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "batched kernel cannot be resident");
     int want = b->tune.blocks_per_sm > 0 ? std::min(b->tune.blocks_per_sm, per_sm) : per_sm;
     *nblocks = std::max(1, std::min(nsm * want, b->ntiles));
@@ -308,10 +423,12 @@ int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
     args[11] = &b->status;
     args[12] = &b->timeout_flag;
     cudaError_t ez = cudaMemsetAsync(b->tile_ctr, 0, 2 * sizeof(int), s);
+    if (ez == cudaSuccess && b->tune.dyn == 2)  // finished-tile counters of the dataflow mode
+        ez = cudaMemsetAsync(b->bar + 2, 0, sizeof(unsigned) * (size_t)b->ncav, s);
     if (ez != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("counter reset: ") + cudaGetErrorString(ez));
     const int npt = npt_of(b->tune);
     const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt) : kernel_ptr<PrecF32P>(npt);
-    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(256), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(block_of(b->tune)), args, 0, s);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -322,6 +439,7 @@ template <class R> int upload_descs(lbm_batch b) {
         h[c].gm = b->gm[c];
         h[c].buf[0] = (char*)b->pool + b->off[0][c];
         h[c].buf[1] = (char*)b->pool + b->off[1][c];
+        h[c].ntiles = c < (int)b->cav_tiles.size() ? b->cav_tiles[c] : 0;
         if constexpr (sizeof(R) == 8) h[c].c = b->coef[c].d;
         else h[c].c = b->coef[c].f;
     }
@@ -468,7 +586,7 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
     BI(cudaMalloc(&b->pool, b->pool_bytes));
     BI(cudaMalloc(&b->status, sizeof(int) * ncav));
     BI(cudaMalloc(&b->timeout_flag, sizeof(int)));
-    BI(cudaMalloc(&b->bar, 2 * sizeof(unsigned)));
+    BI(cudaMalloc(&b->bar, (2 + (size_t)ncav) * sizeof(unsigned)));
     BI(cudaMalloc(&b->tile_ctr, 2 * sizeof(int)));
     BI(cudaMalloc(&b->Ls, sizeof(double) * 2 * ncav));
     BI(cudaMalloc(&b->nu_dev, sizeof(double) * 2 * ncav));
@@ -497,9 +615,17 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
 int lbm_batch_step(lbm_batch b, long nsteps) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
-    int rc = run_steps(b, nsteps, b->stream);
-    if (rc == LBM_OK) b->t += nsteps;
-    return rc;
+    // one launch runs at most 2^16 steps: the dataflow mode's per-cavity
+    // finished-tile counters (steps x tiles of a cavity) stay within 32 bits
+    constexpr long kMaxStepsPerLaunch = 1L << 16;
+    for (long left = nsteps; left > 0;) {
+        const long k = left < kMaxStepsPerLaunch ? left : kMaxStepsPerLaunch;
+        int rc = run_steps(b, k, b->stream);
+        if (rc != LBM_OK) return rc;
+        b->t += k;
+        left -= k;
+    }
+    return LBM_OK;
 }
 
 int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold) {
@@ -569,7 +695,8 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     TuneChoice best;
     bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);
     if (!cached) {
-        const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1}};
+        const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1},
+                                 {32, 1}, {32, 2}, {64, 1}};
         const int occ[] = {0, 2};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -578,7 +705,7 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
         const long nsteps = 20;
         for (auto& sh : shapes)
             for (int o : occ)
-            for (int dyn = 0; dyn < 2; ++dyn) {
+            for (int dyn = 0; dyn < 3; ++dyn) {
                 b->tune.tw = sh[0];
                 b->tune.th = sh[1];
                 b->tune.blocks_per_sm = o;
@@ -618,13 +745,14 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
 
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
-    if (tile_w <= 0 || tile_h <= 0 || (tile_w * tile_h != 256 && tile_w * tile_h != 512) ||
-        (tile_w & (tile_w - 1)) != 0 || blocks_per_sm < 0)
-        return bfail(b, LBM_ERR_ARG, "tiles hold 256 or 512 nodes and have a power-of-two width");
+    const int tn = tile_w * tile_h;
+    if (tile_w <= 0 || tile_h <= 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
+        (tile_w & (tile_w - 1)) != 0 || tile_w < 32 || blocks_per_sm < 0)
+        return bfail(b, LBM_ERR_ARG, "tiles hold 32, 64, 256 or 512 nodes, with a power-of-two width >= 32");
     b->tune.tw = tile_w;
     b->tune.th = tile_h;
     b->tune.blocks_per_sm = blocks_per_sm;
-    b->tune.dyn = dynamic ? 1 : 0;
+    b->tune.dyn = dynamic < 0 || dynamic > 2 ? 0 : dynamic;
     int rc = build_tiles(b);
     if (rc == LBM_OK) rc = grid_size(b, &b->nblocks);
     drop_graph(b);

@@ -52,7 +52,8 @@ def test_batch_matches_single_cavity_bit_for_bit():
     b.close()
 
 
-@pytest.mark.parametrize("tiles", [None, (64, 8, 0, False), (32, 8, 0, True), (128, 4, 2, True)])
+@pytest.mark.parametrize("tiles", [None, (64, 8, 0, 0), (32, 8, 0, 1), (128, 4, 2, 1), (32, 1, 0, 0),
+                                   (32, 2, 0, 1), (64, 1, 0, 0), (32, 1, 0, 2), (32, 2, 0, 2), (128, 4, 0, 2)])
 def test_batch_fp64_matches_oracle(nthreads, tiles):
     from paper_1308_2071_gb300 import Batch
 
@@ -69,6 +70,25 @@ def test_batch_fp64_matches_oracle(nthreads, tiles):
         assert np.abs(np_(f) - fo).max() < 1e-12, k
         assert np.abs(np_(g) - go).max() < 1e-12, k
         assert abs(hot[k] - o.nusselt()[0]) < 1e-10 * abs(hot[k]), k
+    b.close()
+
+
+def test_dataflow_scheduling_is_bit_identical_to_the_single_cavity_kernel():
+    from paper_1308_2071_gb300 import Batch, Cavity
+
+    b = Batch(CAVS, precision="f32")
+    b.set_tiles(32, 1, 0, 2)  # one-warp blocks, one node per thread, per-cavity dependencies
+    b.step(137)
+    b.step(163)
+    rc, st = b.status()
+    assert rc == 0
+    for k, cv in enumerate(CAVS):
+        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision="f32",
+                   nodes_per_thread=1)
+        c.step(300)
+        assert np.array_equal(np_(c.read_state()[0]), np_(b.read_state(k)[0])), k
+        assert np.array_equal(np_(c.read_state()[1]), np_(b.read_state(k)[1])), k
+        c.close()
     b.close()
 
 
