@@ -12,6 +12,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -67,17 +68,14 @@ __device__ __forceinline__ R wall_dT(const Coef<R>& c, const Geom& gm, int x) {
     return gm.thermal_bc == 1 ? c.dTc : (x == 0 ? c.dTh : c.dTc);
 }
 
-// One reverse step: from M^(k+1) and the forward input B_k to M^(k), adding
-// this step's porosity sensitivities to gphi.
+// Reverse of one node for one step: from M^(k+1) and the forward input B_k
+// to M^(k) at (x, y), adding this step's porosity sensitivity to gphi.
 template <class T>
-__global__ void __launch_bounds__(256) k_adjoint(Src<T> state, const typename T::R* __restrict__ Mnext,
-                                                 typename T::R* __restrict__ Mcur,
-                                                 const typename T::P* __restrict__ phi, double* __restrict__ gphi,
-                                                 Geom gm, Coef<typename T::R> c) {
+__device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename T::R* __restrict__ Mnext,
+                                             typename T::R* __restrict__ Mcur, const typename T::P* __restrict__ phi,
+                                             double* __restrict__ gphi, const Geom& gm, const Coef<typename T::R>& c,
+                                             int x, int y) {
     using R = typename T::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= gm.nx || y >= gm.ny) return;
     const int off = y * gm.pitch + x;
     const long k = (long)y * gm.nx + x;
     const Normal nr = normal_of(gm, x, y);
@@ -125,6 +123,19 @@ __global__ void __launch_bounds__(256) k_adjoint(Src<T> state, const typename T:
     gphi[k] += (double)pb;
 }
 
+// One reverse step over every node, grid-stride over a grid sized to the
+// resident capacity (no partial last wave).
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 3 : 1)
+    k_adjoint(Src<T> state, const typename T::R* __restrict__ Mnext, typename T::R* __restrict__ Mcur,
+              const typename T::P* __restrict__ phi, double* __restrict__ gphi, Geom gm, Coef<typename T::R> c) {
+    const long n = (long)gm.nx * gm.ny;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
+        adjoint_node<T>(state, Mnext, Mcur, phi, gphi, gm, c, x, y);
+    }
+}
+
 template <class Out>
 __global__ void k_adj_out(const double* __restrict__ g, Out* __restrict__ out, long n) {
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
@@ -144,7 +155,14 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
     const size_t buf = J.buf_bytes;
     const size_t mbytes = (size_t)gm.plane * NPOP * sizeof(R);
     cudaStream_t s = J.stream;
-    dim3 blk(128, 2), grd((gm.nx + 127) / 128, (gm.ny + 1) / 2);
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 == cudaSuccess) e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<T>, 256, 0);
+    if (e0 != cudaSuccess) return e0;
+    const long nodes = (long)gm.nx * gm.ny;
+    const long want = (long)nsm * (per_sm > 0 ? per_sm : 1);
+    const int nblk = (int)std::max(1L, std::min(want, (nodes + 255) / 256));
     const int nseg = (N + K - 1) / K;
     R* M[2] = {(R*)J.madj, (R*)J.madj + (size_t)gm.plane * NPOP};
     cudaError_t e = cudaMemsetAsync(M[0], 0, mbytes, s);
@@ -178,7 +196,7 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
         }
         for (int j = j0 + len - 1; j >= j0; --j) {
             const Src<T> st = src_view<T>(slot[j - j0], gm.plane);
-            k_adjoint<T><<<grd, blk, 0, s>>>(st, M[a], M[a ^ 1], (const typename T::P*)J.phi, J.gphi, gm, c);
+            k_adjoint<T><<<nblk, 256, 0, s>>>(st, M[a], M[a ^ 1], (const typename T::P*)J.phi, J.gphi, gm, c);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             a ^= 1;
         }
