@@ -140,6 +140,15 @@ int lbm_step(lbm_handle h, long nsteps);
 int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev,
                     void* p_dev);
 
+/* As lbm_nusselt, without waiting: enqueues the computation of (nu_hot,
+ * nu_cold) into out2 (2 doubles) on the handle's stream.  When out2 is device
+ * memory or pinned (mapped) host memory the kernel writes it directly;
+ * otherwise a copy follows the kernel (pageable host memory makes that copy
+ * synchronous).  The values are there once the stream reaches this point
+ * (e.g. after cudaStreamSynchronize or lbm_query).  Lets a caller read the
+ * result of every step without stalling.  Errors: LBM_ERR_ARG (NULL), LBM_ERR_CUDA. */
+int lbm_nusselt_async(lbm_handle h, double* out2);
+
 /* Discrete adjoint (no counterpart in the paper, which has no gradient).
  * Resets the handle to its initial state, runs nsteps steps forward keeping
  * one lattice every ckpt_every steps, evaluates J = mean Nu of the hot wall
@@ -180,14 +189,18 @@ int lbm_field_extrema(lbm_handle h, double* T_max, double* psi_min, double* psi_
  * compare the lattice with a reference implementation.  Stream-ordered. */
 int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev);
 
-/* Checkpoint / resume.  A checkpoint is the handle's two state buffers
- * (the last two post-collision lattices, enough to rebuild every observable
- * and to continue bit-exactly) plus a header (magic, version, nx, ny,
- * precision, t).  lbm_checkpoint_size() gives the byte count; lbm_save()
- * writes it into a caller-owned host buffer of at least that size
- * (synchronises the stream); lbm_load() restores it into a handle created
- * with the same nx, ny and precision.  Errors: LBM_ERR_ARG (buffer too small,
- * header mismatch), LBM_ERR_CUDA. */
+/* Checkpoint / resume.  A checkpoint is a header (magic, version 2, nx, ny,
+ * precision, t) and one state buffer, the post-collision lattice B_{n-1}
+ * that the current post-stream state S_n is pulled from (Eq. 18, 35): every
+ * observable at t_n comes from it, and lbm_load() rebuilds B_n from it with
+ * one step, so a handle that loads it continues exactly as the handle that
+ * saved it would, given the same launch shape (lbm_tune).  Version-1
+ * checkpoints (B_{n-1} then B_n) are still read.  lbm_checkpoint_size() gives
+ * the byte count; lbm_save() writes it into a caller-owned host buffer of at
+ * least that size (synchronises the stream); lbm_load() restores it into a
+ * handle created with the same nx, ny and precision (synchronises the
+ * stream).  Errors: LBM_ERR_ARG (buffer too small, header mismatch),
+ * LBM_ERR_CUDA. */
 int lbm_checkpoint_size(lbm_handle h, size_t* bytes);
 int lbm_save(lbm_handle h, void* host, size_t bytes);
 int lbm_load(lbm_handle h, const void* host, size_t bytes);
@@ -198,7 +211,7 @@ int lbm_load(lbm_handle h, const void* host, size_t bytes);
  * own allocator or to a fixed budget, or a monitoring stage that runs between
  * latency-critical GPU work, where a cudaMalloc would synchronise the device.
  * The caller keeps a checkpoint (the bytes lbm_save writes: header, then the
- * two state buffers) in its own device memory at ckpt_dev, `bytes` long, and
+ * state buffer) in its own device memory at ckpt_dev, `bytes` long, and
  * passes the lbm_params it was made with.  The function computes what
  * lbm_observables computes for that state, except the residual (reported as
  * 0), writes *out (host) and, for each non-NULL pointer, the field (ny*nx

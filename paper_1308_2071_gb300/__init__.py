@@ -7,13 +7,16 @@ Python binding.  Importing the package loads nothing; the first use of the
 library raises if liblbm.so has not been built.
 """
 
-__all__ = ["Cavity", "Batch", "make_params", "build"]
+__all__ = ["Cavity", "Batch", "make_params", "hot_wall_nusselt", "build"]
 
 
 def __getattr__(name):
     if name in ("Cavity", "Batch", "make_params"):
         from . import lbm
         return getattr(lbm, name)
+    if name == "hot_wall_nusselt":
+        from .autograd import hot_wall_nusselt
+        return hot_wall_nusselt
     if name == "build":
         from .build import build
         return build

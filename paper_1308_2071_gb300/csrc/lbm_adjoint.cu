@@ -70,7 +70,9 @@ __device__ __forceinline__ R wall_dT(const Coef<R>& c, const Geom& gm, int x) {
 
 // Reverse of one node for one step: from M^(k+1) and the forward input B_k
 // to M^(k) at (x, y), adding this step's porosity sensitivity to gphi.
-template <class T>
+// RING = false: (x, y) is at least two nodes from every wall, so it is a
+// fluid node and no wall node extrapolates from it.
+template <class T, bool RING>
 __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename T::R* __restrict__ Mnext,
                                              typename T::R* __restrict__ Mcur, const typename T::P* __restrict__ phi,
                                              double* __restrict__ gphi, const Geom& gm, const Coef<typename T::R>& c,
@@ -80,7 +82,7 @@ __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename
     const long k = (long)y * gm.nx + x;
     const Normal nr = normal_of(gm, x, y);
     R lf[9], lh[5];
-    if (nr.dx != 0 || nr.dy != 0) {
+    if (RING && (nr.dx != 0 || nr.dy != 0)) {
         // wall node: it reads no pulled populations of its own; its porosity
         // sensitivity is computed here, its inner neighbour's by that node
 #pragma unroll
@@ -105,6 +107,7 @@ __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename
     R db[9] = {R(0)}, hb[5] = {R(0)}, pb = R(0);
     fluid_node_adjoint<R>(c, t, lf, lh, db, hb, pb);
     // wall nodes b = x - n whose inward normal n points at this node
+    if (RING)
     for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
             if (dx == 0 && dy == 0) continue;
@@ -123,16 +126,40 @@ __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename
     gphi[k] += (double)pb;
 }
 
-// One reverse step over every node, grid-stride over a grid sized to the
-// resident capacity (no partial last wave).
+// One reverse step over the interior nodes (two or more nodes from every
+// wall), grid-stride over a grid sized to the resident capacity.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 1)
     k_adjoint(Src<T> state, const typename T::R* __restrict__ Mnext, typename T::R* __restrict__ Mcur,
               const typename T::P* __restrict__ phi, double* __restrict__ gphi, Geom gm, Coef<typename T::R> c) {
-    const long n = (long)gm.nx * gm.ny;
+    const int w = gm.nx - 4;
+    const long n = (long)w * (gm.ny - 4);
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
-        adjoint_node<T>(state, Mnext, Mcur, phi, gphi, gm, c, x, y);
+        const int yi = (int)(k / w);
+        adjoint_node<T, false>(state, Mnext, Mcur, phi, gphi, gm, c, 2 + (int)(k - (long)yi * w), 2 + yi);
+    }
+}
+
+// The same over the ring of nodes within two of a wall (nx, ny >= 5): rows
+// 0, 1, ny-2, ny-1 in full, then columns 0, 1, nx-2, nx-1 of rows 2..ny-3.
+template <class T>
+__global__ void __launch_bounds__(64)
+    k_adjoint_ring(Src<T> state, const typename T::R* __restrict__ Mnext, typename T::R* __restrict__ Mcur,
+                   const typename T::P* __restrict__ phi, double* __restrict__ gphi, Geom gm,
+                   Coef<typename T::R> c) {
+    const long rows = 4L * gm.nx, n = rows + 4L * (gm.ny - 4);
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        int x, y;
+        if (k < rows) {
+            const int r = (int)(k / gm.nx);
+            x = (int)(k - (long)r * gm.nx);
+            y = r < 2 ? r : gm.ny - 4 + r;
+        } else {
+            const int j = (int)(k - rows), r = j >> 2, q = j & 3;
+            y = 2 + r;
+            x = q < 2 ? q : gm.nx - 4 + q;
+        }
+        adjoint_node<T, true>(state, Mnext, Mcur, phi, gphi, gm, c, x, y);
     }
 }
 
@@ -145,6 +172,24 @@ __global__ void k_adj_out(const double* __restrict__ g, Out* __restrict__ out, l
 }  // namespace lbm
 
 namespace {
+
+// Second stream for the ring kernel, and the two events that join it with
+// the main stream around every reverse step.
+struct RingStream {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t main_done = nullptr, ring_done = nullptr;
+    cudaError_t init() {
+        cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&main_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ring_done, cudaEventDisableTiming);
+        return e;
+    }
+    ~RingStream() {
+        if (ring_done) cudaEventDestroy(ring_done);
+        if (main_done) cudaEventDestroy(main_done);
+        if (s2) cudaStreamDestroy(s2);  // resources go once its work is done
+    }
+};
 
 template <class T>
 cudaError_t adjoint_sweep(const AdjointJob& J) {
@@ -160,9 +205,12 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
     if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e0 == cudaSuccess) e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<T>, 256, 0);
     if (e0 != cudaSuccess) return e0;
-    const long nodes = (long)gm.nx * gm.ny;
-    const long want = (long)nsm * (per_sm > 0 ? per_sm : 1);
-    const int nblk = (int)std::max(1L, std::min(want, (nodes + 255) / 256));
+    const long inner = (long)(gm.nx - 4) * (gm.ny - 4), ring = 4L * gm.nx + 4L * (gm.ny - 4);
+    // one interior block per SM less than fits, so that a 64-thread ring block
+    // finds registers beside the interior blocks and both kernels run at once
+    const long want = (long)nsm * (per_sm > 1 ? per_sm - 1 : 1);
+    const int nblk = (int)std::max(1L, std::min(want, (inner + 255) / 256));
+    const int nring = (int)std::max(1L, std::min((long)nsm, (ring + 63) / 64));
     const int nseg = (N + K - 1) / K;
     R* M[2] = {(R*)J.madj, (R*)J.madj + (size_t)gm.plane * NPOP};
     cudaError_t e = cudaMemsetAsync(M[0], 0, mbytes, s);
@@ -170,6 +218,14 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
     k_adj_seed<R><<<(gm.ny + 255) / 256, 256, 0, s>>>(M[0], gm, J.L, J.dT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(J.gphi, 0, sizeof(double) * (size_t)gm.nx * gm.ny, s)) != cudaSuccess) return e;
+    // Within a reverse step the ring and interior nodes are independent (each
+    // writes its own nodes of M^(k) and gphi), so the ring kernel runs on a
+    // second stream beside the interior kernel; the main stream waits for it
+    // before the next step and before a recompute overwrites the slots.
+    RingStream rs;
+    if ((e = rs.init()) != cudaSuccess) return e;
+    auto join = [&]() { return cudaStreamWaitEvent(s, rs.ring_done, 0); };
+    if ((e = cudaEventRecord(rs.ring_done, rs.s2)) != cudaSuccess) return e;  // nothing pending on s2 yet
     int a = 0;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int j0 = sg * K, len = (N - j0) < K ? (N - j0) : K;
@@ -191,15 +247,29 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
             CoefSet cs;
             if (sizeof(R) == 8) cs.d = *(const Coef<double>*)J.coef;
             else cs.f = *(const Coef<float>*)J.coef;
-            if ((e = launch_step(L, cs)) != cudaSuccess) return e;
+            if ((e = launch_step(L, cs)) != cudaSuccess) break;
             slot[m] = dst;
         }
+        if (e != cudaSuccess) break;
         for (int j = j0 + len - 1; j >= j0; --j) {
             const Src<T> st = src_view<T>(slot[j - j0], gm.plane);
+            // main_done: everything before this step (previous step, recompute) has finished on s
+            if ((e = cudaEventRecord(rs.main_done, s)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(rs.s2, rs.main_done, 0)) != cudaSuccess) break;
+            k_adjoint_ring<T><<<nring, 64, 0, rs.s2>>>(st, M[a], M[a ^ 1], (const typename T::P*)J.phi, J.gphi,
+                                                        gm, c);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = cudaEventRecord(rs.ring_done, rs.s2)) != cudaSuccess) break;
             k_adjoint<T><<<nblk, 256, 0, s>>>(st, M[a], M[a ^ 1], (const typename T::P*)J.phi, J.gphi, gm, c);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = join()) != cudaSuccess) break;
             a ^= 1;
         }
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+        (void)join();  // leave no ring work behind the main stream's back
+        return e;
     }
     const long n = (long)gm.nx * gm.ny;
     if (sizeof(R) == 8) k_adj_out<double><<<kReduceBlocks, 256, 0, s>>>(J.gphi, (double*)J.out, n);

@@ -2,6 +2,7 @@
 // Section 4, state buffers, CUDA-graph replay of long step sequences and the
 // observables round trip.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -40,6 +41,8 @@ struct lbm_handle_s {
     double* obs_dev = nullptr;
     double* obs_host = nullptr;
     int* status_dev = nullptr;
+    unsigned* nu_counter = nullptr;  // block counter of the row-parallel Nusselt kernel
+    double* nu_dev = nullptr;        // its two results
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphExec_t steady_exec = nullptr;
     long steady_key[4] = {0, 0, 0, 0};  // K, parity, max_checks, tol bits
@@ -203,6 +206,8 @@ void free_handle(lbm_handle h) {
     if (h->partials) cudaFree(h->partials);
     if (h->obs_dev) cudaFree(h->obs_dev);
     if (h->status_dev) cudaFree(h->status_dev);
+    if (h->nu_counter) cudaFree(h->nu_counter);
+    if (h->nu_dev) cudaFree(h->nu_dev);
     if (h->obs_host) cudaFreeHost(h->obs_host);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -391,6 +396,9 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     CKI(cudaMalloc(&h->partials, sizeof(double) * 4 * kReduceBlocks));
     CKI(cudaMalloc(&h->obs_dev, sizeof(double) * 8));
     CKI(cudaMalloc(&h->status_dev, sizeof(int)));
+    CKI(cudaMalloc(&h->nu_counter, sizeof(unsigned)));
+    CKI(cudaMemsetAsync(h->nu_counter, 0, sizeof(unsigned), h->stream));
+    CKI(cudaMalloc(&h->nu_dev, 2 * sizeof(double)));
     CKI(cudaMallocHost(&h->obs_host, sizeof(double) * 8));
     const size_t rsz = p->precision == LBM_F64 ? 8 : 4;
     CKI(cudaMalloc(&h->snap, rsz * 2 * (size_t)p->nx * p->ny));
@@ -472,7 +480,7 @@ int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, i
         }
     }
     if (!cached) {
-        const int cand[][3] = {{128, 2, 1}, {64, 4, 1}, {256, 1, 1}, {32, 8, 1}, {128, 1, 2},
+        const int cand[][3] = {{128, 2, 1}, {64, 4, 1},  {256, 1, 1}, {32, 8, 1}, {128, 1, 2},
                                {64, 2, 2},  {128, 2, 2}, {256, 1, 2}, {32, 4, 2}};
         cudaEvent_t e0, e1;
         CK(h, cudaEventCreate(&e0));
@@ -586,8 +594,10 @@ int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void
     return LBM_OK;
 }
 
-int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
-    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+namespace {
+// out: where the kernel writes (nu_hot, nu_cold); device-accessible memory
+int enqueue_nusselt(lbm_handle h, double* out) {
+    if (4 * kReduceBlocks < 2 * ((h->p.ny + 31) / 32)) return fail(h, LBM_ERR_ARG, "too many rows for the reduction");
     ObserveLaunch L;
     memset(&L, 0, sizeof(L));
     L.precision = h->precision;
@@ -597,13 +607,43 @@ int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
     L.L = h->dv.L;
     L.dT = h->dv.dT;
     L.status = h->status_dev;
-    L.out = h->obs_dev;
+    L.out = out;
+    L.counter = h->nu_counter;
     L.stream = h->stream;
     CK(h, launch_nusselt(L, h->coef));
-    CK(h, cudaMemcpyAsync(h->obs_host, h->obs_dev, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+    return LBM_OK;
+}
+}  // namespace
+
+int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    int rc = enqueue_nusselt(h, h->nu_dev);
+    if (rc != LBM_OK) return rc;
+    CK(h, cudaMemcpyAsync(h->obs_host, h->nu_dev, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (nu_hot) *nu_hot = h->obs_host[0];
     if (nu_cold) *nu_cold = h->obs_host[1];
+    return LBM_OK;
+}
+
+int lbm_nusselt_async(lbm_handle h, double* out2) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!out2) return fail(h, LBM_ERR_ARG, "out2 is NULL");
+    // device memory and mapped (pinned) host memory: the kernel writes there
+    // itself; other host memory gets a copy
+    cudaPointerAttributes a;
+    memset(&a, 0, sizeof a);
+    if (cudaPointerGetAttributes(&a, out2) != cudaSuccess) {
+        (void)cudaGetLastError();
+        a.type = cudaMemoryTypeUnregistered;
+    }
+    double* direct = nullptr;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) direct = out2;
+    else if (a.type == cudaMemoryTypeHost && a.devicePointer) direct = (double*)a.devicePointer;
+    if ((uintptr_t)out2 % alignof(double) != 0) direct = nullptr;
+    int rc = enqueue_nusselt(h, direct ? direct : h->nu_dev);
+    if (rc != LBM_OK) return rc;
+    if (!direct) CK(h, cudaMemcpyAsync(out2, h->nu_dev, sizeof(double) * 2, cudaMemcpyDefault, h->stream));
     return LBM_OK;
 }
 
@@ -746,28 +786,27 @@ int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev) {
 
 int lbm_checkpoint_size(lbm_handle h, size_t* bytes) {
     if (!h || !bytes) return fail(h, LBM_ERR_ARG, "handle and bytes are required");
-    *bytes = sizeof(CkptHeader) + 2 * h->buf_bytes;
+    *bytes = sizeof(CkptHeader) + h->buf_bytes;
     return LBM_OK;
 }
 
 int lbm_save(lbm_handle h, void* host, size_t bytes) {
     if (!h || !host) return fail(h, LBM_ERR_ARG, "handle and host buffer are required");
-    size_t need = sizeof(CkptHeader) + 2 * h->buf_bytes;
+    size_t need = sizeof(CkptHeader) + h->buf_bytes;
     if (bytes < need) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
     CkptHeader hd;
     memset(&hd, 0, sizeof hd);
     memcpy(hd.magic, "LBMCKPT", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.nx = h->p.nx;
     hd.ny = h->p.ny;
     hd.precision = h->precision;
     hd.t = h->t;
-    hd.payload = (long)(2 * h->buf_bytes);
+    hd.payload = (long)h->buf_bytes;
     memcpy(host, &hd, sizeof hd);
-    char* dst = (char*)host + sizeof hd;
-    // order: B_{n-1}, then B_n
-    CK(h, cudaMemcpyAsync(dst, h->buf[h->cur ^ 1], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(dst + h->buf_bytes, h->buf[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
+    // B_{n-1} alone: the post-stream state S_n is pulled from it, and B_n is collide(S_n)
+    CK(h, cudaMemcpyAsync((char*)host + sizeof hd, h->buf[h->cur ^ 1], h->buf_bytes, cudaMemcpyDeviceToHost,
+                          h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -777,13 +816,20 @@ int lbm_load(lbm_handle h, const void* host, size_t bytes) {
     CkptHeader hd;
     if (bytes < sizeof hd) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
     memcpy(&hd, host, sizeof hd);
-    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || hd.version != 1) return fail(h, LBM_ERR_ARG, "not a checkpoint");
+    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || (hd.version != 1 && hd.version != 2))
+        return fail(h, LBM_ERR_ARG, "not a checkpoint");
+    const long nbuf = hd.version == 1 ? 2 : 1;
     if (hd.nx != h->p.nx || hd.ny != h->p.ny || hd.precision != h->precision ||
-        hd.payload != (long)(2 * h->buf_bytes) || bytes < sizeof hd + 2 * h->buf_bytes)
+        hd.payload != (long)(nbuf * h->buf_bytes) || bytes < sizeof hd + nbuf * h->buf_bytes)
         return fail(h, LBM_ERR_ARG, "checkpoint does not match this handle");
     const char* src = (const char*)host + sizeof hd;
     CK(h, cudaMemcpyAsync(h->buf[0], src, h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->buf[1], src + h->buf_bytes, h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
+    if (nbuf == 2) {
+        CK(h, cudaMemcpyAsync(h->buf[1], src + h->buf_bytes, h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
+    } else {
+        // B_n = collide(pull(B_{n-1}) + wall rule): the step this handle would have taken
+        CK(h, launch_step(step_launch(h, 0, h->stream), h->coef));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     h->cur = 1;
     h->t = hd.t;

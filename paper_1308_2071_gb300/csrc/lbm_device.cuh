@@ -86,7 +86,15 @@ struct PrecF16 {
     using R = float;
     using P = float;
     static constexpr bool cg = false;
+    static constexpr bool paired = true;  // update_pair computes both nodes with paired FP32 instructions
 };
+template <class T, class = void> struct Paired {
+    static constexpr bool value = false;
+};
+template <class T> struct Paired<T, decltype((void)T::paired)> {
+    static constexpr bool value = T::paired;
+};
+
 // Same arithmetic, L2-only loads (persistent kernels).
 struct PrecF64P : PrecF64 {
     static constexpr bool cg = true;
@@ -119,6 +127,41 @@ template <class T> __host__ __device__ inline Dst<T> dst_view(void* base, int pl
 template <class T> __host__ __device__ constexpr size_t buffer_bytes(int plane) {
     return (size_t)plane * (9 * sizeof(typename T::SF) + 5 * sizeof(typename T::SG));
 }
+
+// ---- two nodes in one register pair ------------------------------------------------
+
+// FP32 values of two nodes side by side.  Each +, -, * is one paired FP32
+// instruction for both nodes (sm_100-class GPUs), rounded to nearest like its
+// scalar counterpart; the pair is never fused into an FMA, so a result may
+// differ from the scalar path's (which the compiler contracts) by a rounding.
+// Division and sqrt are taken per component.  The type and its functions
+// live in a namespace of their own, so that sqrt(float) here keeps meaning
+// the CUDA function while sqrt(F2) is found by argument-dependent lookup.
+namespace x2 {
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float2 a) : v(a) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(double c) : v(make_float2((float)c, (float)c)) {}
+    __device__ __forceinline__ explicit F2(float c) : v(make_float2(c, c)) {}
+    __device__ __forceinline__ explicit F2(int c) : v(make_float2((float)c, (float)c)) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+// a - b = a + (-1) b: the product is exact, so this rounds once, as a subtraction does
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ F2 operator+(float a, F2 b) { return F2(a) + b; }
+__device__ __forceinline__ F2 operator+(F2 a, float b) { return a + F2(b); }
+__device__ __forceinline__ F2 operator-(float a, F2 b) { return F2(a) - b; }
+__device__ __forceinline__ F2 operator-(F2 a, float b) { return a - F2(b); }
+__device__ __forceinline__ F2 operator*(float a, F2 b) { return F2(a) * b; }
+__device__ __forceinline__ F2 operator*(F2 a, float b) { return a * F2(b); }
+__device__ __forceinline__ F2 sqrt(F2 a) { return F2(sqrtf(a.v.x), sqrtf(a.v.y)); }
+}  // namespace x2
+using x2::F2;
 
 // ---- per-launch coefficients ----------------------------------------------------
 
@@ -158,11 +201,11 @@ template <class R> struct Drag {
     R phi, iphi, c_lin, c_quad;
 };
 
-template <class R, bool FIELD, class P>
-__device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field, int off) {
+// Drag coefficients of one cell from its porosity (FIELD) or the uniform ones.
+template <class R, bool FIELD>
+__device__ __forceinline__ Drag<R> drag_of(const Coef<R>& c, R phi) {
     Drag<R> dr;
     if constexpr (FIELD) {
-        R phi = Conv<P, R>::ld(phi_field + off);
         R iphi = R(1) / phi;
         R om = R(1) - phi;
         R ip2 = iphi * iphi;
@@ -177,6 +220,12 @@ __device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field,
         dr.c_quad = c.c_quad;
     }
     return dr;
+}
+
+template <class R, bool FIELD, class P>
+__device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field, int off) {
+    if constexpr (FIELD) return drag_of<R, true>(c, Conv<P, R>::ld(phi_field + off));
+    return drag_of<R, false>(c, R(0));
 }
 
 // ---- pull of one node ------------------------------------------------------------
@@ -216,8 +265,9 @@ template <class R> struct Macro {
 };
 
 // Eq. 36, Section 2 buoyancy, Eq. 22, Eq. 21, Eq. 23, Eq. 4 at a fluid node.
-template <class R>
-__device__ __forceinline__ Macro<R> fluid_macros(const Coef<R>& c, const Drag<R>& dr,
+// CR: type of the coefficients (R, or float for the node pair F2).
+template <class R, class CR>
+__device__ __forceinline__ Macro<R> fluid_macros(const Coef<CR>& c, const Drag<R>& dr,
                                                  const R (&d)[9], const R (&h)[5]) {
     Macro<R> m;
     m.dT = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
@@ -249,8 +299,8 @@ __device__ __forceinline__ Macro<R> fluid_macros(const Coef<R>& c, const Drag<R>
 // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4));
 // Eq. 34 with n_eq of Eq. 29 and Psi of Eq. 30, then g+ = N^-1 n+ (Eq. 35,
 // N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h.
-template <class R>
-__host__ __device__ __forceinline__ void collide(const Coef<R>& c, R iphi, const Macro<R>& mc, R (&d)[9],
+template <class R, class CR>
+__host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, const Macro<R>& mc, R (&d)[9],
                                         R (&h)[5]) {
     // m = M d (Eq. 9-11), as a deviation from the rest moments
     const R a = (d[1] + d[2]) + (d[3] + d[4]);
@@ -444,6 +494,51 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
 }
 
+// Two fluid nodes from their pulled values in one pass of F2 arithmetic (FP32
+// arithmetic types only): about half the arithmetic instructions of two nodes.
+template <class T>
+__device__ __forceinline__ void collide_fluid_pair_x2(const Coef<float>& c, const Geom& gm, const Dst<T>& dst,
+                                                      const float (&a0)[9], const float (&b0)[5],
+                                                      const float (&a1)[9], const float (&b1)[5],
+                                                      const Drag<float>& r0, const Drag<float>& r1, int off0,
+                                                      int off1, int* status) {
+    Drag<F2> dr;
+    dr.phi = F2(r0.phi, r1.phi);
+    dr.iphi = F2(r0.iphi, r1.iphi);
+    dr.c_lin = F2(r0.c_lin, r1.c_lin);
+    dr.c_quad = F2(r0.c_quad, r1.c_quad);
+    F2 d[9], h[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = F2(a0[i], a1[i]);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) h[j] = F2(b0[j], b1[j]);
+    const Macro<F2> m = fluid_macros<F2>(c, dr, d, h);
+    if (!(m.umag.v.x < 0.5f) || !(m.umag.v.y < 0.5f)) atomicOr(status, 1);
+    collide<F2>(c, dr.iphi, m, d, h);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off0, d[i].v.x);
+        Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off1, d[i].v.y);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x);
+        Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off1, h[j].v.y);
+    }
+}
+
+template <class T, bool FIELD>
+__device__ __forceinline__ void update_fluid_pair_x2(const Coef<float>& c, const Geom& gm, const Src<T>& src,
+                                                     const Dst<T>& dst, const typename T::P* phi, int off0, int off1,
+                                                     int* status) {
+    float a0[9], b0[5], a1[9], b1[5];
+    pull<T>(src, gm, off0, a0, b0);
+    pull<T>(src, gm, off1, a1, b1);
+    const Drag<float> r0 = drag_at<float, FIELD, typename T::P>(c, phi, off0);
+    const Drag<float> r1 = drag_at<float, FIELD, typename T::P>(c, phi, off1);
+    collide_fluid_pair_x2<T>(c, gm, dst, a0, b0, a1, b1, r0, r1, off0, off1, status);
+}
+
 // Two nodes at once: when both are fluid nodes all 28 loads are issued before
 // any arithmetic (twice the bytes in flight of one node per thread); nodes
 // outside the lattice (valid = false) or on walls take the one-node path.
@@ -454,6 +549,12 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
     using R = typename T::R;
     const bool f0 = v0 && x0 > 0 && x0 < gm.nx - 1 && y0 > 0 && y0 < gm.ny - 1;
     const bool f1 = v1 && x1 > 0 && x1 < gm.nx - 1 && y1 > 0 && y1 < gm.ny - 1;
+    if constexpr (Paired<T>::value) {
+        if (f0 && f1) {
+            update_fluid_pair_x2<T, FIELD>(c, gm, src, dst, phi, y0 * gm.pitch + x0, y1 * gm.pitch + x1, status);
+            return;
+        }
+    }
     if (f0 && f1) {
         R d0[9], h0[5], d1[9], h1[5];
         const int off0 = y0 * gm.pitch + x0, off1 = y1 * gm.pitch + x1;

@@ -22,7 +22,7 @@ struct Derived {
 int setup_lattice(const lbm_params* p, Derived* dv, struct CoefSet* cs, Geom* gm, std::string* why);
 
 // Header of a checkpoint (lbm_save / lbm_load); the payload that follows is
-// the two state buffers, B_{n-1} then B_n.
+// B_{n-1} (version 2), or B_{n-1} then B_n (version 1, still read).
 struct CkptHeader {
     char magic[8];
     int version, nx, ny, precision;
@@ -68,6 +68,7 @@ struct ObserveLaunch {
     double L, dT;
     const int* status;
     double* out;            // 7 doubles
+    unsigned* counter = nullptr;  // launch_nusselt: zero-initialised block counter
     cudaStream_t stream;
 };
 

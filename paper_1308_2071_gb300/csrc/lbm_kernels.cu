@@ -119,6 +119,62 @@ __global__ void __launch_bounds__(1024) k_finish(Src<T> prev, Geom gm, Coef<type
     }
 }
 
+// Row-parallel mean Nusselt numbers (Eq. 38): one thread per wall row in
+// one-warp blocks (so the rows' scattered loads spread over many SMs), warp
+// sums into partials; the last block to finish folds the partials in a fixed
+// order (deterministic), writes out[0..1] and re-arms the counter.
+template <class T>
+__global__ void __launch_bounds__(32) k_nusselt_rows(Src<T> prev, Geom gm, Coef<typename T::R> c, double L,
+                                                     double dT, double* __restrict__ partials,
+                                                     unsigned* __restrict__ counter, double* __restrict__ out) {
+    __shared__ bool last;
+    double a = 0.0, b = 0.0;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y < gm.ny) {
+        double tl[5], tr[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
+            tr[k] = (double)node_dT<T>(c, gm, prev, gm.nx - 1 - k, y);
+        }
+        const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
+        const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
+        const double wt = (y == 0 || y == gm.ny - 1) ? 0.5 : 1.0;
+        a = wt * (-L * dl / dT);
+        b = wt * (-L * dr / dT);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = 0.0;
+    b = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) {
+        a += __ldcg(partials + 2 * k);
+        b += __ldcg(partials + 2 * k + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = a / (double)(gm.ny - 1);
+        out[1] = b / (double)(gm.ny - 1);
+        *counter = 0u;
+    }
+}
+
 // Full FP64 populations of the post-stream state, dense [q][ny][nx].
 template <class T, bool FIELD>
 __global__ void __launch_bounds__(256) k_read_state(Src<T> prev, const typename T::P* __restrict__ phi, Geom gm,
@@ -202,9 +258,10 @@ static cudaError_t launch_observe_t(const ObserveLaunch& L, const CoefSet& cs) {
 
 template <class T>
 static cudaError_t launch_nusselt_t(const ObserveLaunch& L, const CoefSet& cs) {
-    // npart = 0: only the Nusselt part of the finisher runs
-    k_finish<T><<<1, 1024, 0, L.stream>>>(src_view<T>(L.prev, L.gm.plane), L.gm, coef_of<T>(cs), L.partials, 0,
-                                          L.L, L.dT, L.status, L.out);
+    // partials holds 2 doubles per block; counter is zero between launches
+    const int nb = (L.gm.ny + 31) / 32;
+    k_nusselt_rows<T><<<nb, 32, 0, L.stream>>>(src_view<T>(L.prev, L.gm.plane), L.gm, coef_of<T>(cs), L.L, L.dT,
+                                                L.partials, L.counter, L.out);
     return cudaGetLastError();
 }
 

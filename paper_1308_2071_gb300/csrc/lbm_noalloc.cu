@@ -64,7 +64,7 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
     int rc = setup_lattice(p, &dv, &cs, &gm, &why);
     if (rc != LBM_OK) return fail(rc, why);
     const size_t buf = state_buffer_bytes(p->precision, gm.plane);
-    if (bytes < sizeof(CkptHeader) + 2 * buf) return fail(LBM_ERR_ARG, "checkpoint smaller than this lattice needs");
+    if (bytes < sizeof(CkptHeader) + buf) return fail(LBM_ERR_ARG, "checkpoint smaller than this lattice needs");
 
     double* scratch = nullptr;
     rc = scratch_on_current_device(&scratch);
@@ -75,8 +75,12 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
     cudaError_t e = cudaMemcpyAsync(&hd, ckpt_dev, sizeof hd, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("header read: ") + cudaGetErrorString(e));
-    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || hd.version != 1) return fail(LBM_ERR_ARG, "not a checkpoint");
-    if (hd.nx != p->nx || hd.ny != p->ny || hd.precision != p->precision || hd.payload != (long)(2 * buf))
+    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || (hd.version != 1 && hd.version != 2))
+        return fail(LBM_ERR_ARG, "not a checkpoint");
+    // both versions start with B_{n-1}, the only buffer read here
+    const long nbuf = hd.version == 1 ? 2 : 1;
+    if (hd.nx != p->nx || hd.ny != p->ny || hd.precision != p->precision || hd.payload != (long)(nbuf * buf) ||
+        bytes < sizeof(CkptHeader) + nbuf * buf)
         return fail(LBM_ERR_ARG, "checkpoint does not match the parameters");
 
     double* partials = scratch;

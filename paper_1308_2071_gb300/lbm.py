@@ -149,6 +149,11 @@ class Cavity:
         L.check(L.load().lbm_nusselt(self._h, C.byref(a), C.byref(b)), self._h)
         return a.value, b.value
 
+    def nusselt_async(self, out2_ptr: int):
+        """Enqueues (nu_hot, nu_cold) of the current state into 2 doubles at
+        out2_ptr (pinned host or device memory) without waiting."""
+        L.check(L.load().lbm_nusselt_async(self._h, C.c_void_p(out2_ptr)), self._h)
+
     def read_state(self):
         """Full FP64 post-stream populations f (9, ny, nx) and g (5, ny, nx)."""
         f = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)

@@ -108,3 +108,4 @@ def test_package_import_loads_nothing_and_fails_loudly_without_library(tmp_path)
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+

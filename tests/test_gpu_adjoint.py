@@ -94,3 +94,48 @@ def test_adjoint_requires_a_porosity_field():
     with pytest.raises(_lib.LbmError, match="STATE"):
         cav.adjoint(10, 5)
     cav.close()
+
+
+# ---- torch.autograd.Function ------------------------------------------------------------
+
+def test_autograd_function_gives_the_adjoint_gradient(phi, finite_differences):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity, hot_wall_nusselt
+
+    fd, dirs, j0 = finite_differences
+    cav = Cavity(NX, NY, Ra=RA, Da=DA, phi=PHIBAR, precision="f64", phi_field=torch.from_numpy(phi).cuda())
+    J_ref, g_ref = cav.adjoint(N, K)
+    p = torch.from_numpy(phi).cuda().requires_grad_(True)
+    J = hot_wall_nusselt(p, cav, N, K)
+    assert J.dim() == 0 and float(J) == J_ref  # same launches, same rounding
+    (3.0 * J).backward()
+    assert torch.equal(p.grad, 3.0 * g_ref)
+    g = p.grad.cpu().numpy() / 3.0
+    ad = np.array([g[y, x] for (x, y) in CELLS] + [float((g * v).sum()) for v in dirs])
+    assert np.linalg.norm(ad - fd) / np.linalg.norm(fd) < 1e-6
+    # without requires_grad it is a plain forward run
+    with torch.no_grad():
+        assert float(hot_wall_nusselt(p.detach(), cav, N, K)) == J_ref
+    cav.close()
+
+
+def test_autograd_backward_detects_a_changed_cavity(phi):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity, hot_wall_nusselt
+
+    cav = Cavity(NX, NY, Ra=RA, Da=DA, phi=PHIBAR, precision="f32", phi_field=torch.from_numpy(phi).cuda())
+    p = torch.from_numpy(phi).float().cuda().requires_grad_(True)
+    J = hot_wall_nusselt(p, cav, 40, 16)
+    J.backward()
+    assert p.grad.dtype == torch.float32 and torch.isfinite(p.grad).all()
+    p.grad = None
+    J = hot_wall_nusselt(p, cav, 40, 16)
+    cav.close()
+    cav2 = Cavity(NX, NY, Ra=10 * RA, Da=DA, phi=PHIBAR, precision="f32", phi_field=p.detach())
+    # rebinding the recorded cavity to another one with other parameters must be caught
+    J.grad_fn.cavity = cav2
+    with pytest.raises(RuntimeError, match="changed between forward and backward"):
+        J.backward()
+    cav2.close()
