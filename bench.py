@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed device leg")
+    ap.add_argument("--field", action="store_true",
+                    help="the heterogeneous workload (log-normal porosity field) at --size, for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--leg", default=None, choices=["batched", "adjoint", "heterogeneous", "e2e"],
                     help="run only this extra leg and print its result (profiling)")
@@ -69,10 +71,10 @@ def kernel_sources_digest():
     return hsh.hexdigest()[:16]
 
 
-def recorded_traffic(precision, n):
+def recorded_traffic(precision, n, field=False):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     if the kernel sources are the ones that were measured; else None."""
-    path = os.path.join(ROOT, "profiles", f"k_step_{precision}_{n}.md")
+    path = os.path.join(ROOT, "profiles", f"k_step_{precision}_{n}{'_field' if field else ''}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -87,10 +89,21 @@ def recorded_traffic(precision, n):
         return None
 
 
-def workload(n):
+def workload(n, field=False):
+    if field:
+        return dict(workload=f"side-heated porous cavity {n}x{n}, log-normal permeability field (correlation "
+                             f"length 32 cells, seed 1308, porosity clipped to [0.3, 0.9])", nx=n, ny=n, Ra=1e5,
+                    Da=1e-4, phi=0.6, Pr=1.0, Ma=0.1,
+                    boundary="NEE walls, hot left / cold right / adiabatic top-bottom",
+                    inputs_vs_L2="state larger than L2 (no flush needed)" if n >= 1024 else "L2-resident")
     return dict(workload=f"side-heated porous cavity {n}x{n}", nx=n, ny=n, Ra=1e6, Da=1e-4, phi=0.4,
                 Pr=1.0, Ma=0.1, boundary="NEE walls, hot left / cold right / adiabatic top-bottom",
                 inputs_vs_L2="state larger than L2 (no flush needed)" if n >= 1024 else "L2-resident")
+
+
+def field_bytes(precision):
+    """Bytes of the per-cell porosity read per node-step (its storage type)."""
+    return 8 if precision == "f64" else 4
 
 
 def load_peaks():
@@ -188,13 +201,19 @@ def replica_mlups(nodes_per_rank, steps, ms_max, world):
 TUNE_CACHE = os.path.join(ROOT, "paper_1308_2071_gb300", "_build", "tune_cache.txt")
 
 
-def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=True, shapes=None):
+def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=True, shapes=None, field=False):
     import torch
 
     from paper_1308_2071_gb300 import Cavity
 
-    w = workload(n)
-    cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=precision, Pr=w["Pr"], Ma=w["Ma"])
+    w = workload(n, field)
+    phi = None
+    if field:
+        from paper_1308_2071_gb300.inputs import porosity_field
+
+        phi = torch.from_numpy(porosity_field(n, n, phi_bar=0.6, corr_len=32.0, seed=1308)).cuda()
+    cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=precision, Pr=w["Pr"], Ma=w["Ma"],
+                 phi_field=phi)
     shape = cav.tune(TUNE_CACHE)  # the library's autotuner (cached per lattice); resets to t = 0
     if shapes is not None:
         shapes[precision] = dict(block=[shape[0], shape[1]], nodes_per_thread=shape[2])
@@ -314,6 +333,7 @@ def adjoint_leg(n=512, nsteps=2000, ckpt=100):
 
     phi = torch.from_numpy(perturbed_porosity(n, n, phi_bar=0.6, amplitude=0.05, corr_len=8.0, seed=2000))
     cav = Cavity(n, n, Ra=1e5, Da=1e-2, phi=0.6, precision="f32", phi_field=phi.cuda())
+    cav.tune(TUNE_CACHE)  # launch shape of the forward and recomputing steps
     cav.adjoint(50, 10)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -435,24 +455,27 @@ def main():
         print(json.dumps({"leg": a.leg, a.leg: legs[a.leg]()}), flush=True)
         return
     shapes = {}
-    ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local, shapes=shapes)
+    ms, obs, clocks = device_leg(a.size, a.precision, a.steps, a.warmup, world, gpu_index=local, shapes=shapes,
+                                 field=a.field)
     ms = max_over_ranks(ms, world)
     nodes = a.size * a.size
     mlups = replica_mlups(nodes, a.steps, ms, world)
     peak, peak_kind = load_peaks()
     per_launch_s = ms * 1e-3 / a.steps
-    achieved = nodes * BYTES_PER_NODE[a.precision] / per_launch_s / 1e9
+    bpn = BYTES_PER_NODE[a.precision] + (field_bytes(a.precision) if a.field else 0)
+    achieved = nodes * bpn / per_launch_s / 1e9
     roof = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
-                frac=round(achieved / peak, 4), traffic=recorded_traffic(a.precision, a.size), kernel="k_step",
-                algorithmic_bytes_per_launch=nodes * BYTES_PER_NODE[a.precision], peak_source=peak_kind)
+                frac=round(achieved / peak, 4),
+                traffic=recorded_traffic(a.precision, a.size, a.field), kernel="k_step",
+                algorithmic_bytes_per_launch=nodes * bpn, peak_source=peak_kind)
     line = dict(metric=METRIC, value=round(mlups, 2), unit="MLUPS", n_gpus=world, steps=a.steps,
                 warmup=a.warmup, ms_per_step=round(ms / a.steps, 5), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype=DTYPE[a.precision], data="synthetic (seeded, no dataset)",
-                config=dict(w, parallelism="replicas" if world > 1 else "single GPU",
+                config=dict(workload(a.size, a.field), parallelism="replicas" if world > 1 else "single GPU",
                             global_batch=world, seq_len=None),
                 roofline=roof, clocks=clocks, gpu_launches=a.steps, launch_shape=shapes.get(a.precision),
                 nu_hot_at_end=obs["nu_hot"], status=obs["status"])
-    if rank == 0 and not a.no_extras:
+    if rank == 0 and not a.no_extras and not a.field:  # the extra legs belong to the default workload
         variants = {}
         # FP64 and FP16 storage on the same lattice, and Nu against FP64 at equal steps
         k = min(a.steps, 1000)

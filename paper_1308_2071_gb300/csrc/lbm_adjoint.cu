@@ -240,8 +240,9 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
             L.dst = dst;
             L.phi = J.phi;
             L.gm = gm;
-            L.bx = 128;
-            L.by = 2;
+            L.bx = J.bx;
+            L.by = J.by;
+            L.npt = J.npt;
             L.status = J.status;
             L.stream = s;
             CoefSet cs;

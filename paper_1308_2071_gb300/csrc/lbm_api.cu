@@ -709,6 +709,9 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
         A.L = h->dv.L;
         A.dT = h->dv.dT;
         A.out = dJdphi_dev;
+        A.bx = h->bx;  // the handle's (tuned) launch shape, as in the forward sweep
+        A.by = h->by;
+        A.npt = h->npt;
         A.stream = h->stream;
         e = launch_adjoint_sweep(A);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -104,6 +104,7 @@ struct AdjointJob {
     int* status;
     double L, dT;
     void* out;  // ny*nx dense, double (FP64) or float (FP32)
+    int bx = 128, by = 2, npt = 1;  // launch shape of the recomputing forward steps
     cudaStream_t stream;
 };
 cudaError_t launch_adjoint_sweep(const AdjointJob& J);

@@ -26,8 +26,13 @@ __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const type
 // flight per thread (the FP16-flow variant moves 38 B per node, too few to
 // cover HBM latency with one node per thread).  Wall nodes take the general
 // path one at a time.
+// FP32 arithmetic: at most 64 registers (4 blocks of 256 threads, 8 of 128
+// per SM), which measured faster than the unconstrained 68-80 registers at
+// every size and storage type: more warps keep more loads in flight.  FP64
+// would spill under that limit.
 template <class T, bool FIELD>
-__global__ void __launch_bounds__(256) k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 1)
+    k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
                                                Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y0 = blockIdx.y * (2 * blockDim.y) + threadIdx.y;
