@@ -262,7 +262,8 @@ int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev);
  * block spends at the grid barrier before it records LBM_ERR_TIMEOUT and
  * leaves the kernel; default 2e7.  Also clears a previous timeout. */
 int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
-/* Autotuner: times candidate tile shapes (tile_w x tile_h nodes), blocks per
+/* Autotuner: times candidate tile shapes (tile_w x tile_h nodes, or runs of
+ * tile_w nodes with tile_h = 0), blocks per
  * SM and the two scheduling modes on this batch, keeps the fastest, and records it in a text cache
  * (one line per device, precision and batch shape) at cache_path (NULL: no
  * cache); a cached entry is reused without timing.  Tuning advances the
@@ -270,7 +271,9 @@ int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
 int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm);
 /* Sets the tile shape (tile_w a power of two >= 32; tile_w x tile_h = 256 or
  * 512 nodes run on 256-thread blocks, 32 or 64 nodes on one-warp blocks; the
- * larger size of each pair is two nodes per thread), blocks per SM (0 = as
+ * larger size of each pair is two nodes per thread; tile_h = 0: runs of
+ * tile_w consecutive nodes in each cavity's row-major order, wrapping onto
+ * the next row, so no lanes idle at a cavity's right edge), blocks per SM (0 = as
  * many as fit) and the scheduling without timing: dynamic = 0, each block
  * owns a contiguous run of tiles and a grid barrier ends every step; 1, blocks
  * take chunks of 4 tiles from a per-step counter, same barrier; 2, dataflow:

@@ -70,6 +70,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     return ok_sh != 0;
 }
 
+// Node j of a tile.  lg_tw >= 0: a 2^lg_tw-wide rectangle at (x0, y0), row
+// by row; lg_tw < 0: a run of consecutive nodes in the cavity's row-major
+// order starting at (x0, y0), wrapping onto the next rows (so tiles leave no
+// idle lanes at a cavity's right edge).  Valid when y < ny and x < nx.
+__device__ __forceinline__ void tile_node(const Tile& tl, int lg_tw, int j, int nx, int& x, int& y) {
+    if (lg_tw >= 0) {
+        x = tl.x0 + (j & ((1 << lg_tw) - 1));
+        y = tl.y0 + (j >> lg_tw);
+    } else {
+        x = tl.x0 + j;
+        y = tl.y0;
+        if (x >= nx) {
+            const int q = x / nx;
+            y += q;
+            x -= q * nx;
+        }
+    }
+}
+
 // One launch runs `nsteps` steps of every cavity.  Buffer parity `par` of
 // every cavity holds B_n on entry.
 template <class T, int NPT>
@@ -158,15 +177,15 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
                 const Geom gm = cd.gm;
                 const Src<T> src = src_view<T>(cd.buf[ps], gm.plane);
                 const Dst<T> dst = dst_view<T>(cd.buf[ps ^ 1], gm.plane);
-                const int msk = (1 << lg_tw) - 1;
                 if constexpr (NPT == 2) {
-                    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
-                    const int x0 = tl.x0 + (k0 & msk), y0 = tl.y0 + (k0 >> lg_tw);
-                    const int x1 = tl.x0 + (k1 & msk), y1 = tl.y0 + (k1 >> lg_tw);
+                    int x0, y0, x1, y1;
+                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
+                    tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
                     update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
                                           x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
                 } else {
-                    const int x = tl.x0 + (threadIdx.x & msk), y = tl.y0 + (threadIdx.x >> lg_tw);
+                    int x, y;
+                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x, y);
                     if (x < gm.nx && y < gm.ny)
                         update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
                 }
@@ -214,16 +233,16 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
                 const Geom gm = cd.gm;
                 const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
                 const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
-                // tiles hold blockDim.x * NPT nodes, tile width 2^lg_tw
-                const int msk = (1 << lg_tw) - 1;
+                // tiles hold blockDim.x * NPT nodes
                 if constexpr (NPT == 2) {
-                    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
-                    const int x0 = tl.x0 + (k0 & msk), y0 = tl.y0 + (k0 >> lg_tw);
-                    const int x1 = tl.x0 + (k1 & msk), y1 = tl.y0 + (k1 >> lg_tw);
+                    int x0, y0, x1, y1;
+                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
+                    tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
                     update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
                                           x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
                 } else {
-                    const int x = tl.x0 + (threadIdx.x & msk), y = tl.y0 + (threadIdx.x >> lg_tw);
+                    int x, y;
+                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x, y);
                     if (x < gm.nx && y < gm.ny)
                         update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
                 }
@@ -294,13 +313,16 @@ namespace {
 
 constexpr long long kDefaultWaitPolls = 20000000;  // ~2-20 s of 100 ns polls
 
+// th = 0: linear tiles, runs of tw consecutive nodes in row-major order
 struct TuneChoice {
     int tw = 128, th = 2, blocks_per_sm = 0, dyn = 0;
 };
 
+int tile_nodes(const TuneChoice& t) { return t.th == 0 ? t.tw : t.tw * t.th; }
+
 // Tiles of 256 or 512 nodes run with 256-thread blocks; tiles of 32 or 64
 // nodes with one-warp blocks, whose block synchronisation is a warp's.
-int block_of(const TuneChoice& t) { return t.tw * t.th >= 256 ? 256 : 32; }
+int block_of(const TuneChoice& t) { return tile_nodes(t) >= 256 ? 256 : 32; }
 
 }  // namespace
 
@@ -357,7 +379,7 @@ template <class T> const void* kernel_ptr(int npt) {
     return npt == 2 ? (const void*)&k_batch<T, 2> : (const void*)&k_batch<T, 1>;
 }
 
-int npt_of(const TuneChoice& t) { return t.tw * t.th == 2 * block_of(t) ? 2 : 1; }
+int npt_of(const TuneChoice& t) { return tile_nodes(t) == 2 * block_of(t) ? 2 : 1; }
 
 int log2i(int v) {
     int l = 0;
@@ -371,12 +393,21 @@ int build_tiles(lbm_batch b) {
     if (b->stream) BCK(b, cudaStreamSynchronize(b->stream));  // queued launches may still read the old list
     std::vector<Tile> tl;
     b->cav_tiles.assign(b->ncav, 0);
-    for (int c = 0; c < b->ncav; ++c)
-        for (int y0 = 0; y0 < b->gm[c].ny; y0 += b->tune.th)
-            for (int x0 = 0; x0 < b->gm[c].nx; x0 += b->tune.tw) {
-                tl.push_back(Tile{c, x0, y0});
+    for (int c = 0; c < b->ncav; ++c) {
+        const int nx = b->gm[c].nx, ny = b->gm[c].ny;
+        if (b->tune.th == 0) {
+            for (long k0 = 0; k0 < (long)nx * ny; k0 += b->tune.tw) {
+                tl.push_back(Tile{c, (int)(k0 % nx), (int)(k0 / nx)});
                 ++b->cav_tiles[c];
             }
+        } else {
+            for (int y0 = 0; y0 < ny; y0 += b->tune.th)
+                for (int x0 = 0; x0 < nx; x0 += b->tune.tw) {
+                    tl.push_back(Tile{c, x0, y0});
+                    ++b->cav_tiles[c];
+                }
+        }
+    }
     if (b->tiles) cudaFree(b->tiles);
     b->tiles = nullptr;
     b->ntiles = (int)tl.size();
@@ -405,7 +436,7 @@ int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
     unsigned* cnt = b->bar;
     unsigned* gen = b->bar + 1;
     long long lim = b->wait_limit;
-    int lg = log2i(b->tune.tw), nt = b->ntiles;
+    int lg = b->tune.th == 0 ? -1 : log2i(b->tune.tw), nt = b->ntiles;
     const void* descs = b->descs;
     const Tile* tiles = b->tiles;
     int dyn = b->tune.dyn;
@@ -696,7 +727,7 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);
     if (!cached) {
         const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1},
-                                 {32, 1}, {32, 2}, {64, 1}};
+                                 {32, 1}, {32, 2}, {64, 1}, {32, 0}, {64, 0}, {256, 0}, {512, 0}};
         const int occ[] = {0, 2};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -745,10 +776,11 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
 
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
-    const int tn = tile_w * tile_h;
-    if (tile_w <= 0 || tile_h <= 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
-        (tile_w & (tile_w - 1)) != 0 || tile_w < 32 || blocks_per_sm < 0)
-        return bfail(b, LBM_ERR_ARG, "tiles hold 32, 64, 256 or 512 nodes, with a power-of-two width >= 32");
+    const int tn = tile_h == 0 ? tile_w : tile_w * tile_h;
+    if (tile_w <= 0 || tile_h < 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
+        (tile_h > 0 && ((tile_w & (tile_w - 1)) != 0 || tile_w < 32)) || blocks_per_sm < 0)
+        return bfail(b, LBM_ERR_ARG, "tiles hold 32, 64, 256 or 512 nodes: a power-of-two width >= 32 times "
+                                     "tile_h rows, or tile_h = 0 for runs of tile_w consecutive nodes");
     b->tune.tw = tile_w;
     b->tune.th = tile_h;
     b->tune.blocks_per_sm = blocks_per_sm;

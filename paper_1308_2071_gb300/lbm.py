@@ -267,7 +267,8 @@ class Batch:
         return tw.value, th.value, bps.value
 
     def set_tiles(self, tile_w: int, tile_h: int, blocks_per_sm: int = 0, dynamic: int = 0):
-        """dynamic: 0 static runs of tiles, 1 chunks from a per-step counter,
+        """tile_h = 0: runs of tile_w consecutive nodes in row-major order.
+        dynamic: 0 static runs of tiles, 1 chunks from a per-step counter,
         2 dataflow with per-cavity step dependencies (no grid barrier)."""
         self._check(L.load().lbm_batch_set_tiles(self._b, tile_w, tile_h, blocks_per_sm, int(dynamic)))
 

@@ -52,8 +52,10 @@ def test_batch_matches_single_cavity_bit_for_bit():
     b.close()
 
 
+# (tile_w, tile_h, blocks_per_sm, scheduling); tile_h = 0: runs of tile_w consecutive nodes
 @pytest.mark.parametrize("tiles", [None, (64, 8, 0, 0), (32, 8, 0, 1), (128, 4, 2, 1), (32, 1, 0, 0),
-                                   (32, 2, 0, 1), (64, 1, 0, 0), (32, 1, 0, 2), (32, 2, 0, 2), (128, 4, 0, 2)])
+                                   (32, 2, 0, 1), (64, 1, 0, 0), (32, 1, 0, 2), (32, 2, 0, 2), (128, 4, 0, 2),
+                                   (32, 0, 0, 0), (64, 0, 0, 1), (256, 0, 2, 0), (512, 0, 0, 2)])
 def test_batch_fp64_matches_oracle(nthreads, tiles):
     from paper_1308_2071_gb300 import Batch
 
@@ -73,11 +75,14 @@ def test_batch_fp64_matches_oracle(nthreads, tiles):
     b.close()
 
 
-def test_dataflow_scheduling_is_bit_identical_to_the_single_cavity_kernel():
+@pytest.mark.parametrize("tiles", [(32, 1, 0, 2), (32, 0, 0, 2), (32, 0, 0, 0), (256, 0, 0, 1)])
+def test_one_node_tiles_are_bit_identical_to_the_single_cavity_kernel(tiles):
+    # one node per thread under every scheduling, rectangular or row-run
+    # tiles (the 5 x 7 cavity makes a 32-node run wrap over several rows)
     from paper_1308_2071_gb300 import Batch, Cavity
 
     b = Batch(CAVS, precision="f32")
-    b.set_tiles(32, 1, 0, 2)  # one-warp blocks, one node per thread, per-cavity dependencies
+    b.set_tiles(*tiles)
     b.step(137)
     b.step(163)
     rc, st = b.status()
@@ -92,11 +97,12 @@ def test_dataflow_scheduling_is_bit_identical_to_the_single_cavity_kernel():
     b.close()
 
 
-def test_two_node_tiles_agree_with_the_single_cavity_kernel():
+@pytest.mark.parametrize("tiles", [(32, 16), (64, 0), (512, 0)])
+def test_two_node_tiles_agree_with_the_single_cavity_kernel(tiles):
     from paper_1308_2071_gb300 import Batch, Cavity
 
     b = Batch(CAVS, precision="f32")
-    b.set_tiles(32, 16)
+    b.set_tiles(*tiles)
     b.step(300)
     for k, cv in enumerate(CAVS):
         c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision="f32",
@@ -132,7 +138,8 @@ def test_autotuner_picks_a_shape_and_caches_it(tmp_path):
     b = Batch(CAVS[:4], precision="f32")
     shape = b.tune(cache)
     assert b.query()["t"] == 0  # tuning resets the lattices
-    assert shape[0] * shape[1] in (256, 512)
+    nodes = shape[0] if shape[1] == 0 else shape[0] * shape[1]  # tile_h = 0: a run of tile_w nodes
+    assert nodes in (32, 64, 256, 512)
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and lines[0].split()[1:3] == [str(shape[0]), str(shape[1])]
     b.step(50)
