@@ -408,3 +408,30 @@ def test_nusselt_readback_matches_oracle(precision, tol, shape, nthreads):
         obs = cav.observables()
         assert abs(obs["nu_hot"] - nh) <= 1e-12 * abs(nh)  # other summation order
     cav.close()
+
+
+# ---- config 2 at 1024^2, a long run -----------------------------------------------------
+
+@pytest.fixture(scope="module")
+def oracle_c2_1024(nthreads):
+    """1024^2, Ra = 1e6, Da = 1e-4, phi = 0.4 (the throughput benchmark's physics): the oracle
+    after 2000 steps (about 2e9 node updates)."""
+    o = Oracle(derive(1024, 1024, Ra=1e6, Da=1e-4, phi=0.4))
+    o.step(2000, threads=nthreads)
+    return o.macros(), o.nusselt()
+
+
+@pytest.mark.parametrize("precision,tol_u,tol_T,tol_nu", [
+    ("f64", 1e-10, 1e-10, 1e-10),
+    ("f32", 1e-4, 1e-5, 1e-4),
+])
+def test_config2_1024_long_run_matches_oracle(oracle_c2_1024, precision, tol_u, tol_T, tol_nu):
+    lat = derive(1024, 1024, Ra=1e6, Da=1e-4, phi=0.4)
+    cav = cavity(1024, 1024, Ra=1e6, Da=1e-4, phi=0.4, precision=precision)
+    cav.tune(TUNE_CACHE)
+    cav.step(2000)
+    obs = cav.observables(fields=True)
+    eu, eT, ep, en = field_errors(obs, _Snap(*oracle_c2_1024, lat))
+    assert eu < tol_u and eT < tol_T and en < tol_nu, (precision, eu, eT, ep, en)
+    assert obs["status"] == 0
+    cav.close()
