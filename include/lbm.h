@@ -263,11 +263,12 @@ int lbm_batch_read_state(lbm_batch b, int cav, double* f_dev, double* g_dev);
  * leaves the kernel; default 2e7.  Also clears a previous timeout. */
 int lbm_batch_set_wait_limit(lbm_batch b, long long polls);
 /* Autotuner: times candidate tile shapes (tile_w x tile_h nodes, or runs of
- * tile_w nodes with tile_h = 0), blocks per
- * SM and the two scheduling modes on this batch, keeps the fastest, and records it in a text cache
- * (one line per device, precision and batch shape) at cache_path (NULL: no
- * cache); a cached entry is reused without timing.  Tuning advances the
- * lattices, so the batch is reset to t = 0 afterwards.  Outputs may be NULL. */
+ * tile_w nodes with tile_h = 0), blocks per SM and the three schedules (see
+ * lbm_batch_set_tiles) on this batch, keeps the fastest, and records it in a
+ * text cache (one line per device, precision and batch shape) at cache_path
+ * (NULL: no cache); a cached entry is reused without timing.  Tuning advances
+ * the lattices, so the batch is reset to t = 0 afterwards.  Outputs may be
+ * NULL. */
 int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm);
 /* Sets the tile shape (tile_w a power of two >= 32; tile_w x tile_h = 256 or
  * 512 nodes run on 256-thread blocks, 32 or 64 nodes on one-warp blocks; the
