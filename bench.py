@@ -472,7 +472,7 @@ def main():
                 warmup=a.warmup, ms_per_step=round(ms / a.steps, 5), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype=DTYPE[a.precision], data="synthetic (seeded, no dataset)",
                 config=dict(workload(a.size, a.field), parallelism="replicas" if world > 1 else "single GPU",
-                            global_batch=world, seq_len=None),
+                            replicas=world),
                 roofline=roof, clocks=clocks, gpu_launches=a.steps, launch_shape=shapes.get(a.precision),
                 nu_hot_at_end=obs["nu_hot"], status=obs["status"])
     if rank == 0 and not a.no_extras and not a.field:  # the extra legs belong to the default workload
