@@ -112,8 +112,8 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out);
  * Section 2: K(phi) and F_phi(phi) follow Eq. 5 per cell, with the particle
  * diameter fixed so that K(p->phi) = Da L^2).  phi_dev: device array of ny*nx
  * values in (0, 1), dtype LBM_F64 (double) or LBM_F32 (float); the caller
- * keeps ownership, the library copies it (to float for the FP32 path, to
- * half for the FP16-storage path, double for FP64).  Requires
+ * keeps ownership, the library copies it (to float for the FP32 and
+ * FP16-storage paths, double for FP64).  Requires
  * use_phi_field = 1.  Resets the state to the initial state (t = 0).
  * Errors: LBM_ERR_ARG, LBM_ERR_STATE (use_phi_field = 0), LBM_ERR_CUDA. */
 int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype);
@@ -237,9 +237,11 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
  * precision, LBM_F32 or LBM_F64, uniform porosity) advanced together: every
  * lbm_batch_step() is ONE persistent cooperative kernel launch that runs all
  * requested steps of all cavities (blocks walk a tile list that covers every
- * cavity; a bounded grid-wide barrier separates the steps), captured into a
- * CUDA graph on first use and replayed.  Per node it runs the same code as
- * lbm_step, so each cavity evolves exactly as it would alone. */
+ * cavity; a bounded grid-wide barrier, or in the dataflow schedule bounded
+ * per-cavity step counters, order the steps), captured into a CUDA graph on
+ * first use and replayed.  Per node it runs the same code as lbm_step: with
+ * one node per thread each cavity evolves bit for bit as it would alone with
+ * one node per thread, with two it agrees to FP rounding. */
 typedef struct lbm_batch_s* lbm_batch;
 
 /* p: ncav parameter sets (host); same precision in all.  Initial state as in
@@ -252,7 +254,7 @@ int lbm_batch_step(lbm_batch b, long nsteps);
  * doubles (either may be NULL); synchronises. */
 int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold);
 /* Per-cavity divergence status into status[ncav] (may be NULL); returns
- * LBM_ERR_TIMEOUT if a grid-barrier wait ran out in any step since the last
+ * LBM_ERR_TIMEOUT if a bounded wait (grid barrier or step counter) ran out in any step since the last
  * lbm_batch_set_wait_limit (the lattice is then incomplete), LBM_ERR_DIVERGED
  * if any cavity diverged, else LBM_OK.  Synchronises. */
 int lbm_batch_status(lbm_batch b, int* status);
