@@ -34,11 +34,11 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def run_cases(cases, tol=2e-7, check_every=2000, max_steps=20_000_000):
+def run_cases(cases, tol=2e-7, check_every=2000, max_steps=20_000_000, precision="f32"):
     """cases: list of (n, kwargs).  Returns [(cavity, steps, change)] after
-    running every cavity to steady state concurrently, in FP32 (its Nusselt
-    numbers agree with FP64 to about 3e-5; tol is the relative change of both
-    wall Nusselt numbers over check_every steps)."""
+    running every cavity to steady state concurrently, in FP32 by default (its
+    Nusselt numbers agree with FP64 to about 3e-5; tol is the relative change of
+    both wall Nusselt numbers over check_every steps)."""
     import torch
 
     from paper_1308_2071_gb300 import Cavity
@@ -47,7 +47,7 @@ def run_cases(cases, tol=2e-7, check_every=2000, max_steps=20_000_000):
 
     def work(i, n, kw):
         s = torch.cuda.Stream()
-        cav = Cavity(n, n, precision="f32", stream=s, **kw)
+        cav = Cavity(n, n, precision=precision, stream=s, **kw)
         steps, ch = cav.run_steady(tol, check_every, max_steps)
         out[i] = (cav, steps, ch)
 
@@ -153,3 +153,28 @@ def test_mrt_and_lbgk_at_high_rayleigh():
     assert mrt.query()[1] == 0 and bgk.query()[1] == 0
     assert abs(mrt.nusselt()[1] / 16.4386 - 1) < 0.02
     assert abs(bgk.nusselt()[1] / mrt.nusselt()[1] - 1) < 0.01
+
+
+def test_grid_convergence_of_the_cavity_nusselt_number():
+    # Config 1 physics (Ra = 1e4, Da = 1e-2, phi = 0.6) at steady state on
+    # L = 32, 64, 128, 256 in FP64: the mean of the two walls' Nu converges at
+    # an observed order near 2 on the finer grids (second-order scheme,
+    # Section 1), the walls' difference (the first-order adiabatic
+    # extrapolation) at first order, and the extrapolate matches Table 2's
+    # 1.494 (120^2) to 1 %.
+    ns = (33, 65, 129, 257)
+    res = run_cases([(n, dict(Ra=1e4, Da=1e-2, phi=0.6)) for n in ns], tol=1e-11, check_every=4000,
+                    precision="f64")
+    nu = {}
+    for n, (cav, steps, ch) in zip(ns, res):
+        assert ch < 1e-11, (n, steps, ch)
+        nu[n] = cav.nusselt()
+        cav.close()
+    mean = [0.5 * (nu[n][0] + nu[n][1]) for n in ns]
+    gap = [nu[n][0] - nu[n][1] for n in ns]
+    orders = [math.log2((mean[k] - mean[k + 1]) / (mean[k + 1] - mean[k + 2])) for k in range(2)]
+    assert 1.6 < orders[1] < 2.6, (mean, orders)
+    assert all(1.7 < gap[k] / gap[k + 1] < 2.3 for k in range(3)), gap
+    extrapolated = mean[3] + (mean[3] - mean[2]) / 3.0
+    assert abs(extrapolated / 1.494 - 1) < 0.01, (mean, extrapolated)
+

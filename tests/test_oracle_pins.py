@@ -471,3 +471,30 @@ def test_internal_heating_parameters_follow_the_definitions():
     a4 = 0.2 * (1 / lat4.zeta[1] - 0.5)
     assert abs(lat4.gbeta * lat4.Q * 150 ** 5 / (nu4 * a4 ** 2) / 1e7 - 1) < 1e-12
     assert lat4.T0 == 0.5
+
+
+def _nusselt_at_fixed_time(n, tau, nthreads):
+    """Config 1 physics (Ra = 1e4, Da = 1e-2, phi = 0.6, Pr = 1) on an n^2
+    lattice under diffusive scaling: tau_nu is held fixed, so Ma falls as 1/L
+    (Eq. 37, second occurrence) and one time step is (L/16)^-2 of the L = 16
+    step; 2000 (L/16)^2 steps reach the same physical time on every grid."""
+    L = n - 1
+    Ma = (tau - 0.5) / (L * np.sqrt(3.0)) * np.sqrt(1e4)
+    o = Oracle(derive(n, n, Ra=1e4, Da=1e-2, phi=0.6, Ma=Ma))
+    return o.step(2000 * (L // 16) ** 2, threads=nthreads).nusselt()
+
+
+def test_cavity_nusselt_converges_under_grid_refinement(nthreads):
+    # Second-order scheme (Section 1), checked by refinement at fixed
+    # relaxation times (diffusive scaling) on L = 16, 32, 64: the difference
+    # between the hot- and cold-wall Nusselt numbers, which is zero in the
+    # continuum steady state and which the wall rule leaves on the lattice,
+    # shrinks by about 4 per refinement (3.4, 3.8 measured); the mean of the
+    # two walls changes 6 times less from 33^2 to 65^2 than from 17^2 to 33^2;
+    # the 65^2 mean is within 1 % of Table 2's 1.494 (120^2).
+    nu = {n: _nusselt_at_fixed_time(n, 0.6, nthreads) for n in (17, 33, 65)}
+    mean = {n: 0.5 * (a + b) for n, (a, b) in nu.items()}
+    gap = {n: a - b for n, (a, b) in nu.items()}
+    assert 3.0 < gap[17] / gap[33] < 4.5 and 3.0 < gap[33] / gap[65] < 4.5, gap
+    assert abs(mean[33] - mean[65]) < abs(mean[17] - mean[33]) / 4.0, mean
+    assert abs(mean[65] / 1.494 - 1) < 0.01, mean
