@@ -164,7 +164,8 @@ class Cavity:
         return f, g
 
     def save(self) -> bytearray:
-        """Checkpoint (header + both state buffers) as host bytes."""
+        """Checkpoint as host bytes: a header and the state buffer the current
+        post-stream state is pulled from (lbm_save)."""
         n = C.c_size_t()
         L.check(L.load().lbm_checkpoint_size(self._h, C.byref(n)), self._h)
         buf = bytearray(n.value)
@@ -173,6 +174,7 @@ class Cavity:
         return buf
 
     def load(self, blob: bytearray):
+        """Restores a checkpoint of a cavity with the same nx, ny and precision."""
         ptr = (C.c_char * len(blob)).from_buffer(blob)
         L.check(L.load().lbm_load(self._h, C.addressof(ptr), len(blob)), self._h)
 
