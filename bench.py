@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--field", action="store_true",
                     help="the heterogeneous workload (log-normal porosity field) at --size, for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--leg", default=None, choices=["batched", "adjoint", "heterogeneous", "e2e"],
+    ap.add_argument("--leg", default=None, choices=["batched", "adjoint", "heterogeneous", "e2e", "long_run"],
                     help="run only this extra leg and print its result (profiling)")
     return ap.parse_args()
 
@@ -286,6 +286,40 @@ def e2e_leg(n, precision, steps):
                 seconds=round(t1 - t0, 4), load_seconds=round(t_load - t0, 4))
 
 
+def long_run_leg(n=1024, steps=50000):
+    """Config 2's stated run length at n^2 (Ra 1e6, Da 1e-4, porosity 0.4): FP32
+    and FP16-flow storage against the FP64 path after `steps` steps (the FP64
+    GPU path matches the oracle to 1e-10 over 2000 steps at this size): max
+    velocity error over max |u|, max temperature error over dT, relative error
+    of both wall Nusselt numbers."""
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    w = workload(n)
+    res = {}
+    for prec in ("f64", "f32", "f16"):
+        cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=prec, Pr=w["Pr"], Ma=w["Ma"])
+        cav.tune(TUNE_CACHE)
+        cav.step(steps)
+        o = cav.observables(fields=True)
+        res[prec] = dict(nu=(o["nu_hot"], o["nu_cold"]), ux=o["ux"].double(), uy=o["uy"].double(),
+                         T=o["T"].double())
+        cav.close()
+    ref = res["f64"]
+    umax = max(float(ref["ux"].abs().max()), float(ref["uy"].abs().max()))
+    out = dict(workload=f"{n}x{n}, Ra 1e6, Da 1e-4, phi 0.4, {steps} steps", nu_f64=list(ref["nu"]))
+    for prec in ("f32", "f16"):
+        r = res[prec]
+        out[prec] = dict(
+            err_u_rel_max=max(float((r["ux"] - ref["ux"]).abs().max()), float((r["uy"] - ref["uy"]).abs().max())) / umax,
+            err_T_max_over_dT=float((r["T"] - ref["T"]).abs().max()),
+            err_nu_rel=max(abs(r["nu"][k] - ref["nu"][k]) / abs(ref["nu"][k]) for k in (0, 1)))
+    del res
+    torch.cuda.empty_cache()
+    return out
+
+
 def batched_leg(steps, warmup, ncav=256, seed=2071):
     """Batched sweep: ncav cavities of uneven size (64^2..512^2), log-uniform Ra
     and Da, uniform porosity (seeded draws), FP32, one persistent
@@ -450,7 +484,7 @@ def main():
     _lib.load()
     if a.leg:
         legs = dict(batched=lambda: batched_leg(min(a.steps, 1000), min(a.warmup, 8)),
-                    adjoint=adjoint_leg, heterogeneous=heterogeneous_leg,
+                    adjoint=adjoint_leg, heterogeneous=heterogeneous_leg, long_run=long_run_leg,
                     e2e=lambda: e2e_leg(a.size, a.precision, min(a.steps, 1000)))
         print(json.dumps({"leg": a.leg, a.leg: legs[a.leg]()}), flush=True)
         return
@@ -505,6 +539,7 @@ def main():
         line["batched"] = batched_leg(min(a.steps, 1000), 8)
         line["adjoint"] = adjoint_leg()
         line["heterogeneous"] = heterogeneous_leg()
+        line["long_run_precision"] = long_run_leg()
         mlc, threads, k, dt = cpu_leg(a.size, a.cpu_seconds)
         ml1, _, k1, dt1 = cpu_leg(a.size, 1.0, threads=1)
         line["cpu_baseline"] = dict(value=round(mlc, 3), unit="MLUPS", cores=threads, kind="oracle",
