@@ -40,8 +40,9 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled MLUPS & % HBM roofline, FP32 vs FP64 at stated Nu error; adjoint MLUPS"
 # every population read once and written once: FP64 14 x 8 B, FP32 14 x 4 B,
 # FP16 variant 9 x 2 B (flow) + 5 x 4 B (thermal), each way
-BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4, "f16": 2 * (9 * 2 + 5 * 4)}
-DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16 flow + f32 thermal storage, f32 arithmetic"}
+BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4, "f16": 2 * (9 * 2 + 5 * 4), "f32t": 30 * 4}
+DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16 flow + f32 thermal storage, f32 arithmetic",
+         "f32t": "f32 storage with a per-node temperature frame, f32 arithmetic"}
 
 
 def parse():
@@ -51,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=4096)
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16", "f32t"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed device leg")
     ap.add_argument("--field", action="store_true",
                     help="the heterogeneous workload (log-normal porosity field) at --size, for profiling")
@@ -298,7 +299,7 @@ def long_run_leg(n=1024, steps=50000):
 
     w = workload(n)
     res = {}
-    for prec in ("f64", "f32", "f16"):
+    for prec in ("f64", "f32", "f16", "f32t"):
         cav = Cavity(n, n, Ra=w["Ra"], Da=w["Da"], phi=w["phi"], precision=prec, Pr=w["Pr"], Ma=w["Ma"])
         cav.tune(TUNE_CACHE)
         cav.step(steps)
@@ -309,7 +310,7 @@ def long_run_leg(n=1024, steps=50000):
     ref = res["f64"]
     umax = max(float(ref["ux"].abs().max()), float(ref["uy"].abs().max()))
     out = dict(workload=f"{n}x{n}, Ra 1e6, Da 1e-4, phi 0.4, {steps} steps", nu_f64=list(ref["nu"]))
-    for prec in ("f32", "f16"):
+    for prec in ("f32", "f16", "f32t"):
         r = res[prec]
         out[prec] = dict(
             err_u_rel_max=max(float((r["ux"] - ref["ux"]).abs().max()), float((r["uy"] - ref["uy"]).abs().max())) / umax,
@@ -521,7 +522,7 @@ def main():
         # FP64 and FP16 storage on the same lattice, and Nu against FP64 at equal steps
         k = min(a.steps, 1000)
         nsteps_cmp = a.warmup + k
-        for prec in ("f64", "f16"):
+        for prec in ("f64", "f16", "f32t"):
             ms_p, obs_p, _ = device_leg(a.size, prec, k, a.warmup, 1, gpu_index=local,
                                         sample_clocks=False, shapes=shapes)
             ach = nodes * BYTES_PER_NODE[prec] / (ms_p * 1e-3 / k) / 1e9
@@ -534,6 +535,7 @@ def main():
         variants["f32"] = dict(nu_hot=obs32["nu_hot"], at_step=nsteps_cmp)
         variants["nu_rel_err_f32_vs_f64"] = abs(obs32["nu_hot"] - nu64) / abs(nu64)
         variants["nu_rel_err_f16_vs_f64"] = abs(variants["f16"]["nu_hot"] - nu64) / abs(nu64)
+        variants["nu_rel_err_f32t_vs_f64"] = abs(variants["f32t"]["nu_hot"] - nu64) / abs(nu64)
         line["variants"] = variants
         line["e2e"] = e2e_leg(a.size, a.precision, min(a.steps, 1000))
         line["batched"] = batched_leg(min(a.steps, 1000), 8)

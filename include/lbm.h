@@ -41,6 +41,10 @@ extern "C" {
 #define LBM_F64 0            /* FP64 storage, FP64 arithmetic                       */
 #define LBM_F32 1            /* FP32 storage of deviations, FP32 arithmetic         */
 #define LBM_F32_STORE_F16 2  /* FP16 storage of deviations, FP32 arithmetic         */
+#define LBM_F32_FRAMED 3     /* FP32 storage, thermal populations relative to a per-
+                                node temperature frame (one more plane), FP32
+                                arithmetic: resolves slow late-time evolution that
+                                plain FP32 storage of g_j - w~_j T0 loses           */
 
 /* thermal boundary layouts */
 #define LBM_BC_SIDE_HEATED 0 /* Section 4.1: left T_h, right T_c, top/bottom adiabatic */
@@ -63,7 +67,7 @@ typedef struct {
     double sigma, varpi; /* thermal capacity ratio, D2Q5 constant (Section 4: 1, -2) */
     double Th, Tc;       /* wall temperatures; T0 = (Th + Tc) / 2                      */
     double Qppp;         /* internal heat source Q''' in lattice units (Eq. 30, 33-36) */
-    int precision;       /* LBM_F64, LBM_F32, LBM_F32_STORE_F16                         */
+    int precision;       /* LBM_F64, LBM_F32, LBM_F32_STORE_F16, LBM_F32_FRAMED         */
     int use_phi_field;   /* 0: uniform phi; 1: per-cell phi from lbm_set_porous_field  */
     int forchheimer;     /* 1: F_phi of Eq. 5; 0: F_phi = 0 (Brinkman model, Sect. 3.1)*/
     int thermal_bc;      /* LBM_BC_SIDE_HEATED or LBM_BC_COOLED                          */

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(6)
-LBM_F64, LBM_F32, LBM_F32_STORE_F16 = 0, 1, 2
+LBM_F64, LBM_F32, LBM_F32_STORE_F16, LBM_F32_FRAMED = 0, 1, 2, 3
 LBM_BC_SIDE_HEATED, LBM_BC_COOLED = 0, 1
 LBM_MRT, LBM_LBGK = 0, 1
 

@@ -84,7 +84,7 @@ int derive(const lbm_params* p, Derived* dv, std::string* why) {
     if (!(p->sigma > 0.0) || !(p->varpi < 1.0) || !(p->varpi > -4.0))
         return *why = "sigma must be positive and varpi in (-4, 1)", LBM_ERR_ARG;
     if (!(p->Th > p->Tc)) return *why = "Th must exceed Tc (with LBM_BC_COOLED, Th - Tc is the scale dT)", LBM_ERR_ARG;
-    if (p->precision < LBM_F64 || p->precision > LBM_F32_STORE_F16) return *why = "bad precision", LBM_ERR_ARG;
+    if (p->precision < LBM_F64 || p->precision > LBM_F32_FRAMED) return *why = "bad precision", LBM_ERR_ARG;
     if (p->use_phi_field && !(p->phi < 1.0))
         return *why = "a porosity field needs a mean porosity below 1", LBM_ERR_ARG;
     if (p->adiabatic_order != 1 && p->adiabatic_order != 2) return *why = "adiabatic_order is 1 or 2", LBM_ERR_ARG;
@@ -174,7 +174,7 @@ int setup_lattice(const lbm_params* p, Derived* dv, CoefSet* cs, Geom* gm, std::
     if (rc != LBM_OK) return rc;
     // row pitch in elements: rows of the flow planes and of the thermal planes
     // both start on 128-byte boundaries (FP64: 16, FP32: 32, FP16 flow: 64)
-    const int align = p->precision == LBM_F64 ? 16 : (p->precision == LBM_F32 ? 32 : 64);
+    const int align = p->precision == LBM_F64 ? 16 : (p->precision == LBM_F32_STORE_F16 ? 64 : 32);
     const long pitch = ((long)p->nx + align - 1) / align * align;
     const long plane = pitch * (long)p->ny;
     if (plane * NPOP >= (1L << 31)) return *why = "lattice too large for 32-bit offsets", LBM_ERR_ARG;
@@ -650,7 +650,8 @@ int lbm_nusselt_async(lbm_handle h, double* out2) {
 int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void* dJdphi_dev) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "the adjoint needs a handle created with use_phi_field = 1");
-    if (h->precision == LBM_F32_STORE_F16) return fail(h, LBM_ERR_ARG, "the adjoint runs in LBM_F64 or LBM_F32");
+    if (h->precision != LBM_F64 && h->precision != LBM_F32)
+        return fail(h, LBM_ERR_ARG, "the adjoint runs in LBM_F64 or LBM_F32");
     if (h->p.adiabatic_order != 1) return fail(h, LBM_ERR_ARG, "the adjoint supports first-order adiabatic walls");
     if (nsteps < 1 || ckpt_every < 1 || !dJdphi_dev) return fail(h, LBM_ERR_ARG, "need nsteps >= 1, ckpt_every >= 1, output");
     const long N = nsteps, K = ckpt_every < nsteps ? ckpt_every : nsteps;

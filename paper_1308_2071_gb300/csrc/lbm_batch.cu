@@ -585,6 +585,10 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
             delete b;
             return bfail(nullptr, LBM_ERR_ARG, "every cavity of a batch needs the same precision");
         }
+        if (prec != LBM_F32 && prec != LBM_F64) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_ARG, "a batch runs in LBM_F32 or LBM_F64");
+        }
         if (p[c].use_phi_field) {
             delete b;
             return bfail(nullptr, LBM_ERR_ARG, "batched cavities use uniform porosity");

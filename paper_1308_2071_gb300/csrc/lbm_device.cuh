@@ -95,6 +95,21 @@ template <class T> struct Paired<T, decltype((void)T::paired)> {
     static constexpr bool value = T::paired;
 };
 
+// FP32 storage with a per-node temperature frame: a fifteenth plane holds
+// F(x), the node's T - T0 rounded to FP32 when the node was last written, and
+// the thermal planes hold g_j - w~_j (T0 + F(x)) instead of g_j - w~_j T0.  The
+// stored thermal values are then the small non-equilibrium parts, so FP32
+// resolves the per-step change of T even where |T - T0| is near 1/2.
+struct PrecF32T : PrecF32 {
+    static constexpr bool framed = true;
+};
+template <class T, class = void> struct Framed {
+    static constexpr bool value = false;
+};
+template <class T> struct Framed<T, decltype((void)T::framed)> {
+    static constexpr bool value = T::framed;
+};
+
 // Same arithmetic, L2-only loads (persistent kernels).
 struct PrecF64P : PrecF64 {
     static constexpr bool cg = true;
@@ -103,29 +118,34 @@ struct PrecF32P : PrecF32 {
     static constexpr bool cg = true;
 };
 
-// Read-only typed view of one state buffer: 9 flow planes then 5 thermal planes.
+// Read-only typed view of one state buffer: 9 flow planes then 5 thermal
+// planes (then, for framed storage, the frame plane t).
 template <class T> struct Src {
     const typename T::SF* __restrict__ f;
     const typename T::SG* __restrict__ g;
+    const typename T::SG* __restrict__ t;
 };
 template <class T> struct Dst {
     typename T::SF* __restrict__ f;
     typename T::SG* __restrict__ g;
+    typename T::SG* __restrict__ t;
 };
 template <class T> __host__ __device__ inline Src<T> src_view(const void* base, int plane) {
     Src<T> s;
     s.f = (const typename T::SF*)base;
     s.g = (const typename T::SG*)((const char*)base + (size_t)9 * plane * sizeof(typename T::SF));
+    s.t = s.g + (size_t)5 * plane;
     return s;
 }
 template <class T> __host__ __device__ inline Dst<T> dst_view(void* base, int plane) {
     Dst<T> d;
     d.f = (typename T::SF*)base;
     d.g = (typename T::SG*)((char*)base + (size_t)9 * plane * sizeof(typename T::SF));
+    d.t = d.g + (size_t)5 * plane;
     return d;
 }
 template <class T> __host__ __device__ constexpr size_t buffer_bytes(int plane) {
-    return (size_t)plane * (9 * sizeof(typename T::SF) + 5 * sizeof(typename T::SG));
+    return (size_t)plane * (9 * sizeof(typename T::SF) + (Framed<T>::value ? 6 : 5) * sizeof(typename T::SG));
 }
 
 // ---- two nodes in one register pair ------------------------------------------------
@@ -254,6 +274,34 @@ __device__ __forceinline__ typename T::R pull_heat(const Src<T>& src, const Geom
     return t;
 }
 
+// Framed storage: thermal values pulled into node off were stored in the
+// frames of the nodes they came from; re-express them in this node's frame F
+// (add w~_j (F(x - e_j) - F), j >= 1: nearby FP32 frames subtract exactly) and
+// return F.
+template <class T>
+__device__ __forceinline__ typename T::R frame_in(const Src<T>& src, const Geom& gm, int off, typename T::R wt1,
+                                                  typename T::R (&h)[5]) {
+    using R = typename T::R;
+    const R F = Conv<typename T::SG, R, T::cg>::ld(src.t + off);
+#pragma unroll
+    for (int j = 1; j < 5; ++j)
+        h[j] += wt1 * (Conv<typename T::SG, R, T::cg>::ld(src.t + off - ey9(j) * gm.pitch - ex9(j)) - F);
+    return F;
+}
+
+// T - T0 - F(x) at node off from the pulled thermal values (framed storage), and F(x).
+template <class T>
+__device__ __forceinline__ typename T::R pull_heat_framed(const Src<T>& src, const Geom& gm, int off,
+                                                          typename T::R wt1, typename T::R& F) {
+    using R = typename T::R;
+    R h[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        h[j] = Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+    F = frame_in<T>(src, gm, off, wt1, h);
+    return h[0] + h[1] + h[2] + h[3] + h[4];
+}
+
 // ---- macroscopic values -------------------------------------------------------------
 
 template <class R> struct Macro {
@@ -262,15 +310,24 @@ template <class R> struct Macro {
     R dT;      // T - T0 (Eq. 36)
     R Fx, Fy;  // total force (Eq. 4)
     R umag;    // |u|
+    R F, dTl;  // framed storage: the node's frame and T - T0 - F (else 0 and dT)
 };
 
 // Eq. 36, Section 2 buoyancy, Eq. 22, Eq. 21, Eq. 23, Eq. 4 at a fluid node.
-// CR: type of the coefficients (R, or float for the node pair F2).
-template <class R, class CR>
+// CR: type of the coefficients (R, or float for the node pair F2).  FR: the
+// thermal values h are relative to the frame F (framed storage).
+template <class R, class CR, bool FR = false>
 __device__ __forceinline__ Macro<R> fluid_macros(const Coef<CR>& c, const Drag<R>& dr,
-                                                 const R (&d)[9], const R (&h)[5]) {
+                                                 const R (&d)[9], const R (&h)[5], R F = R(0)) {
     Macro<R> m;
-    m.dT = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+    if constexpr (FR) {
+        m.F = F;
+        m.dTl = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+        m.dT = F + m.dTl;
+    } else {
+        m.dT = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+        m.dTl = m.dT;
+    }
     const R Gy = c.gbeta * m.dT;
     const R jx = (d[1] - d[3]) + (d[5] - d[6]) - (d[7] - d[8]);
     const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
@@ -299,7 +356,7 @@ __device__ __forceinline__ Macro<R> fluid_macros(const Coef<CR>& c, const Drag<R
 // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4));
 // Eq. 34 with n_eq of Eq. 29 and Psi of Eq. 30, then g+ = N^-1 n+ (Eq. 35,
 // N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h.
-template <class R, class CR>
+template <class R, class CR, bool FR = false>
 __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, const Macro<R>& mc, R (&d)[9],
                                         R (&h)[5]) {
     // m = M d (Eq. 9-11), as a deviation from the rest moments
@@ -367,8 +424,11 @@ __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, cons
     const R T = c.T0 + mc.dT;
     const R ne1 = ux * T * c.inv_sigma;
     const R ne2 = uy * T * c.inv_sigma;
-    const R ne3 = c.varpi * mc.dT;
-    const R q0 = (n0 - c.z[0] * (n0 - mc.dT) + c.hz[0] * c.psi0) * R(0.2);
+    // framed storage: n and the conserved part of n_eq are taken relative to
+    // T0 + F, the flux part (u T / sigma) uses the absolute T
+    const R dTn = FR ? mc.dTl : mc.dT;
+    const R ne3 = c.varpi * dTn;
+    const R q0 = (n0 - c.z[0] * (n0 - dTn) + c.hz[0] * c.psi0) * R(0.2);
     const R q1 = (n1 - c.z[1] * (n1 - ne1)) * R(0.5);
     const R q2 = (n2 - c.z[2] * (n2 - ne2)) * R(0.5);
     const R q3 = (n3 - c.z[3] * (n3 - ne3) + c.hz[3] * c.psi3) * R(0.05);
@@ -405,11 +465,17 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
                                                           const Drag<typename T::R>& drb,
                                                           typename T::R (&d)[9], typename T::R (&h)[5]) {
     using R = typename T::R;
+    constexpr bool FR = Framed<T>::value;
     const int offf = (y + nr.dy) * gm.pitch + (x + nr.dx);
     R df[9], hf[5];
     pull<T>(src, gm, offf, df, hf);
+    R Ff = R(0), Fb = R(0);  // frames of the inner neighbour and of this wall node
+    if constexpr (FR) {
+        Ff = frame_in<T>(src, gm, offf, c.wt1, hf);
+        Fb = Conv<typename T::SG, R, T::cg>::ld(src.t + y * gm.pitch + x);
+    }
     const Drag<R> drf = drag_at<R, FIELD, typename T::P>(c, phi_field, offf);
-    const Macro<R> mf = fluid_macros<R>(c, drf, df, hf);
+    const Macro<R> mf = fluid_macros<R, R, FR>(c, drf, df, hf, Ff);
 
     Macro<R> mb;
     mb.ux = R(0);
@@ -422,14 +488,30 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
         mb.dP = mf.dP;
     }
     const bool dirichlet = (gm.thermal_bc == 1) || (nr.dx != 0);
-    if (dirichlet) {
-        mb.dT = (gm.thermal_bc == 1) ? c.dTc : (x == 0 ? c.dTh : c.dTc);
-    } else if (gm.adi_order == 2) {
-        const int offff = (y + 2 * nr.dy) * gm.pitch + (x + 2 * nr.dx);
-        const R dTff = pull_heat<T>(src, gm, offff) + c.qhalf;
-        mb.dT = (R(4) * mf.dT - dTff) * R(1.0 / 3.0);
+    if constexpr (FR) {
+        // the wall temperature relative to this node's frame, from differences of nearby frames
+        mb.F = Fb;
+        if (dirichlet) {
+            mb.dTl = ((gm.thermal_bc == 1) ? c.dTc : (x == 0 ? c.dTh : c.dTc)) - Fb;
+        } else if (gm.adi_order == 2) {
+            const int offff = (y + 2 * nr.dy) * gm.pitch + (x + 2 * nr.dx);
+            R Fff;
+            const R dTlff = pull_heat_framed<T>(src, gm, offff, c.wt1, Fff) + c.qhalf;
+            mb.dTl = (R(4) * ((Ff - Fb) + mf.dTl) - ((Fff - Fb) + dTlff)) * R(1.0 / 3.0);
+        } else {
+            mb.dTl = (Ff - Fb) + mf.dTl;
+        }
+        mb.dT = Fb + mb.dTl;
     } else {
-        mb.dT = mf.dT;
+        if (dirichlet) {
+            mb.dT = (gm.thermal_bc == 1) ? c.dTc : (x == 0 ? c.dTh : c.dTc);
+        } else if (gm.adi_order == 2) {
+            const int offff = (y + 2 * nr.dy) * gm.pitch + (x + 2 * nr.dx);
+            const R dTff = pull_heat<T>(src, gm, offff) + c.qhalf;
+            mb.dT = (R(4) * mf.dT - dTff) * R(1.0 / 3.0);
+        } else {
+            mb.dT = mf.dT;
+        }
     }
     mb.Fx = R(0);
     mb.Fy = drb.phi * c.gbeta * mb.dT;
@@ -447,15 +529,20 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
         const R cP = (i == 0) ? R(-5.0 / 3.0) : R(3.0 * w9(i));
         d[i] = df[i] - si + cP * ddP;
     }
-    // g_b = g_eq(T_b, 0) + g_f - g_eq(T_f, u_f) (Eq. 37, first occurrence)
+    // g_b = g_eq(T_b, 0) + g_f - g_eq(T_f, u_f) (Eq. 37, first occurrence); framed:
+    // T_b - T_f from the frames' difference and the local parts, the result
+    // re-expressed in this node's frame
     const R Tf = c.T0 + mf.dT;
-    const R ddT = mb.dT - mf.dT;
+    // (framed: w~ (T_b - T_f) + w~ (F_f - F_b) = w~ (dTl_b - dTl_f))
+    const R ddT = FR ? mb.dTl - mf.dTl : mb.dT - mf.dT;
     const R adv = Tf * c.inv_sigma * c.inv_csT2 * c.wt1;
-    h[0] = hf[0] + c.wt0 * ddT;
-    h[1] = hf[1] + c.wt1 * ddT - adv * ux;
-    h[2] = hf[2] + c.wt1 * ddT - adv * uy;
-    h[3] = hf[3] + c.wt1 * ddT + adv * ux;
-    h[4] = hf[4] + c.wt1 * ddT + adv * uy;
+    const R sh0 = c.wt0 * ddT;
+    const R sh1 = c.wt1 * ddT;
+    h[0] = hf[0] + sh0;
+    h[1] = hf[1] + sh1 - adv * ux;
+    h[2] = hf[2] + sh1 - adv * uy;
+    h[3] = hf[3] + sh1 + adv * ux;
+    h[4] = hf[4] + sh1 + adv * uy;
     return mb;
 }
 
@@ -471,9 +558,28 @@ __device__ __forceinline__ Macro<typename T::R> node_state(const Coef<typename T
     const Normal nr = normal_of(gm, x, y);
     if (nr.dx == 0 && nr.dy == 0) {
         pull<T>(src, gm, off, d, h);
+        if constexpr (Framed<T>::value) {
+            const R F = frame_in<T>(src, gm, off, c.wt1, h);
+            return fluid_macros<R, R, true>(c, dr, d, h, F);
+        }
         return fluid_macros<R>(c, dr, d, h);
     }
     return wall_node<T, FIELD>(c, gm, src, phi_field, x, y, nr, dr, d, h);
+}
+
+// Framed storage: re-expresses the collided thermal values, relative to the
+// frame mc.F they were computed in, in the node's new frame fl(T - T0) and
+// stores that frame.
+template <class T>
+__device__ __forceinline__ void frame_out(const Coef<typename T::R>& c, const Geom& gm, const Dst<T>& dst, int off,
+                                          const Macro<typename T::R>& mc, typename T::R (&h)[5]) {
+    using R = typename T::R;
+    const R Fn = mc.dT;           // F + dTl rounded: the new frame
+    const R shift = Fn - mc.F;    // exact for nearby values
+    h[0] -= c.wt0 * shift;
+#pragma unroll
+    for (int j = 1; j < 5; ++j) h[j] -= c.wt1 * shift;
+    Conv<typename T::SG, R, T::cg>::st(dst.t + off, Fn);
 }
 
 // One node of the step: pull (or wall rule), collide, store.
@@ -486,8 +592,9 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     Drag<R> dr;
     const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
     if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
-    collide<R>(c, dr.iphi, mc, d, h);
+    collide<R, R, Framed<T>::value>(c, dr.iphi, mc, d, h);
     const int off = y * gm.pitch + x;
+    if constexpr (Framed<T>::value) frame_out<T>(c, gm, dst, off, mc, h);
 #pragma unroll
     for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
 #pragma unroll
@@ -558,15 +665,25 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
     if (f0 && f1) {
         R d0[9], h0[5], d1[9], h1[5];
         const int off0 = y0 * gm.pitch + x0, off1 = y1 * gm.pitch + x1;
+        constexpr bool FR = Framed<T>::value;
         pull<T>(src, gm, off0, d0, h0);
         pull<T>(src, gm, off1, d1, h1);
+        R F0 = R(0), F1 = R(0);
+        if constexpr (FR) {
+            F0 = frame_in<T>(src, gm, off0, c.wt1, h0);
+            F1 = frame_in<T>(src, gm, off1, c.wt1, h1);
+        }
         const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
         const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
-        const Macro<R> m0 = fluid_macros<R>(c, dr0, d0, h0);
-        const Macro<R> m1 = fluid_macros<R>(c, dr1, d1, h1);
+        const Macro<R> m0 = fluid_macros<R, R, FR>(c, dr0, d0, h0, F0);
+        const Macro<R> m1 = fluid_macros<R, R, FR>(c, dr1, d1, h1, F1);
         if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
-        collide<R>(c, dr0.iphi, m0, d0, h0);
-        collide<R>(c, dr1.iphi, m1, d1, h1);
+        collide<R, R, FR>(c, dr0.iphi, m0, d0, h0);
+        collide<R, R, FR>(c, dr1.iphi, m1, d1, h1);
+        if constexpr (FR) {
+            frame_out<T>(c, gm, dst, off0, m0, h0);
+            frame_out<T>(c, gm, dst, off1, m1, h1);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
@@ -584,21 +701,39 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
 }
 
 // T - T0 of the post-stream state at node (x, y), pulled from B_{n-1}
-// (the wall rule's temperature on wall nodes).
+// (the wall rule's temperature on wall nodes), in FP64 (framed storage adds
+// the frame to the local part in FP64, so the value keeps its precision).
 template <class T>
-__device__ __forceinline__ typename T::R node_dT(const Coef<typename T::R>& c, const Geom& gm,
-                                                 const Src<T>& prev, int x, int y) {
+__device__ __forceinline__ double node_dT(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& prev, int x,
+                                          int y) {
     using R = typename T::R;
     const Normal nr = normal_of(gm, x, y);
-    if (nr.dx == 0 && nr.dy == 0) return pull_heat<T>(prev, gm, y * gm.pitch + x) + c.qhalf;
-    if (gm.thermal_bc == 1) return c.dTc;
-    if (nr.dx != 0) return x == 0 ? c.dTh : c.dTc;
-    const R dTf = pull_heat<T>(prev, gm, (y + nr.dy) * gm.pitch + x) + c.qhalf;
-    if (gm.adi_order == 2) {
-        const R dTff = pull_heat<T>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x) + c.qhalf;
-        return (R(4) * dTf - dTff) * R(1.0 / 3.0);
+    if constexpr (Framed<T>::value) {
+        R F;
+        if (nr.dx == 0 && nr.dy == 0) {
+            const R l = pull_heat_framed<T>(prev, gm, y * gm.pitch + x, c.wt1, F) + c.qhalf;
+            return (double)F + (double)l;
+        }
+        if (gm.thermal_bc == 1) return (double)c.dTc;
+        if (nr.dx != 0) return (double)(x == 0 ? c.dTh : c.dTc);
+        const R lf = pull_heat_framed<T>(prev, gm, (y + nr.dy) * gm.pitch + x, c.wt1, F) + c.qhalf;
+        if (gm.adi_order == 2) {
+            R Fff;
+            const R lff = pull_heat_framed<T>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x, c.wt1, Fff) + c.qhalf;
+            return (4.0 * ((double)F + (double)lf) - ((double)Fff + (double)lff)) / 3.0;
+        }
+        return (double)F + (double)lf;
+    } else {
+        if (nr.dx == 0 && nr.dy == 0) return (double)(pull_heat<T>(prev, gm, y * gm.pitch + x) + c.qhalf);
+        if (gm.thermal_bc == 1) return (double)c.dTc;
+        if (nr.dx != 0) return (double)(x == 0 ? c.dTh : c.dTc);
+        const R dTf = pull_heat<T>(prev, gm, (y + nr.dy) * gm.pitch + x) + c.qhalf;
+        if (gm.adi_order == 2) {
+            const R dTff = pull_heat<T>(prev, gm, (y + 2 * nr.dy) * gm.pitch + x) + c.qhalf;
+            return (double)((R(4) * dTf - dTff) * R(1.0 / 3.0));
+        }
+        return (double)dTf;
     }
-    return dTf;
 }
 
 // Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).

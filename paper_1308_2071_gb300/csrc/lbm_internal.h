@@ -35,7 +35,7 @@ void set_global_error(const std::string& msg);
 
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8; fixed so FP64 sums are reproducible
 
-enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2 };
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_F32T = 3 };
 
 // Coefficients of one lattice in both arithmetic types.
 struct CoefSet {

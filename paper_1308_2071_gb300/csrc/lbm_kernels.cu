@@ -194,12 +194,14 @@ __global__ void __launch_bounds__(256) k_read_state(Src<T> prev, const typename 
         const int y = (int)(k / gm.nx), x = (int)(k - (long)y * gm.nx);
         R d[9], h[5];
         Drag<R> dr;
-        (void)node_state<T, FIELD>(c, gm, prev, phi, x, y, dr, d, h);
+        const Macro<R> mc = node_state<T, FIELD>(c, gm, prev, phi, x, y, dr, d, h);
+        // framed storage: h is relative to T0 + F (F = 0 otherwise)
+        const double Tr = Framed<T>::value ? T0 + (double)mc.F : T0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i * n + k] = w9(i) + (double)d[i];
-        g[k] = wt0 * T0 + (double)h[0];
+        g[k] = wt0 * Tr + (double)h[0];
 #pragma unroll
-        for (int j = 1; j < 5; ++j) g[j * n + k] = wt1 * T0 + (double)h[j];
+        for (int j = 1; j < 5; ++j) g[j * n + k] = wt1 * Tr + (double)h[j];
     }
 }
 
@@ -218,6 +220,7 @@ template <class T> static const Coef<typename T::R>& coef_of(const CoefSet& cs);
 template <> const Coef<double>& coef_of<PrecF64>(const CoefSet& cs) { return cs.d; }
 template <> const Coef<float>& coef_of<PrecF32>(const CoefSet& cs) { return cs.f; }
 template <> const Coef<float>& coef_of<PrecF16>(const CoefSet& cs) { return cs.f; }
+template <> const Coef<float>& coef_of<PrecF32T>(const CoefSet& cs) { return cs.f; }
 
 template <class T>
 static cudaError_t launch_step_t(const StepLaunch& L, const CoefSet& cs) {
@@ -285,6 +288,7 @@ static cudaError_t launch_read_state_t(const ReadStateLaunch& L, const CoefSet& 
     switch (prec) {                                     \
         case PREC_F64: return fn<PrecF64>(__VA_ARGS__); \
         case PREC_F32: return fn<PrecF32>(__VA_ARGS__); \
+        case PREC_F32T: return fn<PrecF32T>(__VA_ARGS__); \
         default: return fn<PrecF16>(__VA_ARGS__);       \
     }
 
@@ -303,6 +307,7 @@ size_t state_buffer_bytes(int precision, int plane) {
     switch (precision) {
         case PREC_F64: return buffer_bytes<PrecF64>(plane);
         case PREC_F32: return buffer_bytes<PrecF32>(plane);
+        case PREC_F32T: return buffer_bytes<PrecF32T>(plane);
         default: return buffer_bytes<PrecF16>(plane);
     }
 }

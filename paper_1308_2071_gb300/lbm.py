@@ -12,7 +12,7 @@ import torch
 
 from . import _lib as L
 
-PRECISIONS = {"f64": L.LBM_F64, "f32": L.LBM_F32, "f16": L.LBM_F32_STORE_F16}
+PRECISIONS = {"f64": L.LBM_F64, "f32": L.LBM_F32, "f16": L.LBM_F32_STORE_F16, "f32t": L.LBM_F32_FRAMED}
 
 
 def make_params(nx: int, ny: int, Ra: float, Da: float, phi: float, precision: str = "f32",
