@@ -238,7 +238,7 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
 
 /* ---- batched sweep ---------------------------------------------------------
  * Many independent cavities (each its own nx, ny, Ra, Da, porosity, ...; one
- * precision, LBM_F32 or LBM_F64, uniform porosity) advanced together: every
+ * precision, LBM_F32, LBM_F32_FRAMED or LBM_F64, uniform porosity) advanced together: every
  * lbm_batch_step() is ONE persistent cooperative kernel launch that runs all
  * requested steps of all cavities (blocks walk a tile list that covers every
  * cavity; a bounded grid-wide barrier, or in the dataflow schedule bounded

@@ -379,6 +379,12 @@ template <class T> const void* kernel_ptr(int npt) {
     return npt == 2 ? (const void*)&k_batch<T, 2> : (const void*)&k_batch<T, 1>;
 }
 
+const void* batch_kernel(int precision, int npt) {
+    if (precision == LBM_F64) return kernel_ptr<PrecF64P>(npt);
+    if (precision == LBM_F32_FRAMED) return kernel_ptr<PrecF32TP>(npt);
+    return kernel_ptr<PrecF32P>(npt);
+}
+
 int npt_of(const TuneChoice& t) { return tile_nodes(t) == 2 * block_of(t) ? 2 : 1; }
 
 int log2i(int v) {
@@ -421,7 +427,7 @@ int grid_size(lbm_batch b, int* nblocks) {
     int dev = 0, nsm = 0, per_sm = 0;
     BCK(b, cudaGetDevice(&dev));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt_of(b->tune)) : kernel_ptr<PrecF32P>(npt_of(b->tune));
+    const void* k = batch_kernel(b->precision, npt_of(b->tune));
     BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_of(b->tune), 0));
     if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "batched kernel cannot be resident");
     int want = b->tune.blocks_per_sm > 0 ? std::min(b->tune.blocks_per_sm, per_sm) : per_sm;
@@ -458,7 +464,7 @@ int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
         ez = cudaMemsetAsync(b->bar + 2, 0, sizeof(unsigned) * (size_t)b->ncav, s);
     if (ez != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("counter reset: ") + cudaGetErrorString(ez));
     const int npt = npt_of(b->tune);
-    const void* k = b->precision == LBM_F64 ? kernel_ptr<PrecF64P>(npt) : kernel_ptr<PrecF32P>(npt);
+    const void* k = batch_kernel(b->precision, npt);
     cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(block_of(b->tune)), args, 0, s);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
     return LBM_OK;
@@ -564,7 +570,8 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
     *out = nullptr;
     if (!p || ncav <= 0) return bfail(nullptr, LBM_ERR_ARG, "need at least one cavity");
     const int prec = p[0].precision;
-    if (prec != LBM_F32 && prec != LBM_F64) return bfail(nullptr, LBM_ERR_ARG, "batched cavities run in FP32 or FP64");
+    if (prec != LBM_F32 && prec != LBM_F64 && prec != LBM_F32_FRAMED)
+        return bfail(nullptr, LBM_ERR_ARG, "batched cavities run in LBM_F32, LBM_F32_FRAMED or LBM_F64");
     lbm_batch b = new lbm_batch_s();
     b->ncav = ncav;
     b->precision = prec;
@@ -584,10 +591,6 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
         if (p[c].precision != prec) {
             delete b;
             return bfail(nullptr, LBM_ERR_ARG, "every cavity of a batch needs the same precision");
-        }
-        if (prec != LBM_F32 && prec != LBM_F64) {
-            delete b;
-            return bfail(nullptr, LBM_ERR_ARG, "a batch runs in LBM_F32 or LBM_F64");
         }
         if (p[c].use_phi_field) {
             delete b;
@@ -669,6 +672,9 @@ int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold) {
     if (b->precision == LBM_F64)
         k_batch_nusselt<PrecF64P><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<double>*)b->descs, prev, b->Ls,
                                                                  b->nu_dev);
+    else if (b->precision == LBM_F32_FRAMED)
+        k_batch_nusselt<PrecF32TP><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
+                                                                  b->nu_dev);
     else
         k_batch_nusselt<PrecF32P><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
                                                                  b->nu_dev);

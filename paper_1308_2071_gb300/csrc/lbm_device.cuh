@@ -117,6 +117,9 @@ struct PrecF64P : PrecF64 {
 struct PrecF32P : PrecF32 {
     static constexpr bool cg = true;
 };
+struct PrecF32TP : PrecF32P {
+    static constexpr bool framed = true;
+};
 
 // Read-only typed view of one state buffer: 9 flow planes then 5 thermal
 // planes (then, for framed storage, the frame plane t).

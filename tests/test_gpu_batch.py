@@ -75,20 +75,23 @@ def test_batch_fp64_matches_oracle(nthreads, tiles):
     b.close()
 
 
-@pytest.mark.parametrize("tiles", [(32, 1, 0, 2), (32, 0, 0, 2), (32, 0, 0, 0), (256, 0, 0, 1)])
-def test_one_node_tiles_are_bit_identical_to_the_single_cavity_kernel(tiles):
+@pytest.mark.parametrize("tiles,precision", [((32, 1, 0, 2), "f32"), ((32, 0, 0, 2), "f32"),
+                                             ((32, 0, 0, 0), "f32"), ((256, 0, 0, 1), "f32"),
+                                             ((32, 1, 0, 2), "f32t"), ((256, 1, 0, 0), "f32t")])
+def test_one_node_tiles_are_bit_identical_to_the_single_cavity_kernel(tiles, precision):
     # one node per thread under every scheduling, rectangular or row-run
-    # tiles (the 5 x 7 cavity makes a 32-node run wrap over several rows)
+    # tiles (the 5 x 7 cavity makes a 32-node run wrap over several rows),
+    # plain and framed FP32 storage
     from paper_1308_2071_gb300 import Batch, Cavity
 
-    b = Batch(CAVS, precision="f32")
+    b = Batch(CAVS, precision=precision)
     b.set_tiles(*tiles)
     b.step(137)
     b.step(163)
     rc, st = b.status()
     assert rc == 0
     for k, cv in enumerate(CAVS):
-        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision="f32",
+        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision=precision,
                    nodes_per_thread=1)
         c.step(300)
         assert np.array_equal(np_(c.read_state()[0]), np_(b.read_state(k)[0])), k
