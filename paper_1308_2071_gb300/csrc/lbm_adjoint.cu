@@ -245,6 +245,7 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
             L.npt = J.npt;
             L.status = J.status;
             L.stream = s;
+            L.pdl = m > 1;  // directly behind the previous recomputing step
             CoefSet cs;
             if (sizeof(R) == 8) cs.d = *(const Coef<double>*)J.coef;
             else cs.f = *(const Coef<float>*)J.coef;

@@ -545,8 +545,10 @@ int lbm_step(lbm_handle h, long nsteps) {
         CK(h, cudaGraphLaunch(h->gexec[h->cur], h->stream));
         left -= kGraphSteps;  // even count: cur unchanged
     }
-    for (; left > 0; --left) {
-        CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
+    for (long k = 0; left > 0; --left, ++k) {
+        StepLaunch Ls = step_launch(h, h->cur, h->stream);
+        Ls.pdl = k > 0;  // directly behind the previous step kernel
+        CK(h, launch_step(Ls, h->coef));
         h->cur ^= 1;
     }
     h->t += nsteps;
@@ -679,10 +681,13 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
         e = cudaMemsetAsync(ckpt, 0, h->buf_bytes, h->stream);  // j = 0: the rest state B_{-1}
         for (long t = 0; t < N && e == cudaSuccess; ++t) {
             const long j = t + 1;  // buf[cur] holds B_t, state index j
-            if (j % K == 0 && j <= N - 1)
+            const bool copy = j % K == 0 && j <= N - 1;
+            if (copy)
                 e = cudaMemcpyAsync((char*)ckpt + (size_t)(j / K) * h->buf_bytes, h->buf[h->cur], h->buf_bytes,
                                     cudaMemcpyDeviceToDevice, h->stream);
-            if (e == cudaSuccess) e = launch_step(step_launch(h, h->cur, h->stream), h->coef);
+            StepLaunch Ls = step_launch(h, h->cur, h->stream);
+            Ls.pdl = t > 0 && !copy;  // directly behind the previous step kernel
+            if (e == cudaSuccess) e = launch_step(Ls, h->coef);
             h->cur ^= 1;
         }
         h->t = N;

@@ -53,6 +53,7 @@ struct StepLaunch {
     int npt = 1;  // nodes per thread along y (1 or 2)
     int* status;
     cudaStream_t stream;
+    bool pdl = false;  // launch as a programmatic dependent of the previous step
 };
 
 struct ObserveLaunch {

@@ -12,9 +12,18 @@ namespace lbm {
 // wall rule on perimeter nodes (Section 4), collides (Eq. 17, 34) and writes
 // the node's post-collision populations to the other buffer.  The buffer
 // pair alternates, so dst holds B_{n+1} when src holds B_n.
+//
+// Launched as a programmatic dependent of the previous step (back-to-back
+// steps of small lattices), a block starts while that step drains and waits
+// here until it has completed and its writes are visible: the step reads the
+// whole previous lattice and rewrites the buffer the previous step read.
+// Without that launch attribute the wait returns at once.
+__device__ __forceinline__ void wait_for_previous_step() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class T, bool FIELD>
 __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
                                               Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+    wait_for_previous_step();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= gm.nx || y >= gm.ny) return;
@@ -34,6 +43,7 @@ template <class T, bool FIELD>
 __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 1)
     k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
                                                Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+    wait_for_previous_step();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y0 = blockIdx.y * (2 * blockDim.y) + threadIdx.y;
     const int y1 = y0 + blockDim.y;
@@ -222,27 +232,38 @@ template <> const Coef<float>& coef_of<PrecF32>(const CoefSet& cs) { return cs.f
 template <> const Coef<float>& coef_of<PrecF16>(const CoefSet& cs) { return cs.f; }
 template <> const Coef<float>& coef_of<PrecF32T>(const CoefSet& cs) { return cs.f; }
 
+// Launches kernel k with the step's arguments, as a programmatic dependent of
+// the previous work on the stream when L.pdl is set.
+template <class T, class K>
+static cudaError_t launch_one_step(K k, dim3 grd, dim3 blk, const StepLaunch& L, const Src<T>& s, const Dst<T>& d,
+                                   const typename T::P* phi, const Coef<typename T::R>& c) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = L.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, s, d, phi, L.gm, c, L.status);
+}
+
 template <class T>
 static cudaError_t launch_step_t(const StepLaunch& L, const CoefSet& cs) {
     dim3 blk(L.bx, L.by);
     const Src<T> s = src_view<T>(L.src, L.gm.plane);
     const Dst<T> d = dst_view<T>(L.dst, L.gm.plane);
+    const typename T::P* phi = (const typename T::P*)L.phi;
     if (L.npt == 2) {
         dim3 grd2((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + 2 * L.by - 1) / (2 * L.by));
-        if (L.phi)
-            k_step2<T, true><<<grd2, blk, 0, L.stream>>>(s, d, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
-                                                        L.status);
-        else
-            k_step2<T, false><<<grd2, blk, 0, L.stream>>>(s, d, nullptr, L.gm, coef_of<T>(cs), L.status);
-        return cudaGetLastError();
+        if (L.phi) return launch_one_step<T>(k_step2<T, true>, grd2, blk, L, s, d, phi, coef_of<T>(cs));
+        return launch_one_step<T>(k_step2<T, false>, grd2, blk, L, s, d, nullptr, coef_of<T>(cs));
     }
     dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
-    if (L.phi)
-        k_step<T, true><<<grd, blk, 0, L.stream>>>(s, d, (const typename T::P*)L.phi, L.gm, coef_of<T>(cs),
-                                                  L.status);
-    else
-        k_step<T, false><<<grd, blk, 0, L.stream>>>(s, d, nullptr, L.gm, coef_of<T>(cs), L.status);
-    return cudaGetLastError();
+    if (L.phi) return launch_one_step<T>(k_step<T, true>, grd, blk, L, s, d, phi, coef_of<T>(cs));
+    return launch_one_step<T>(k_step<T, false>, grd, blk, L, s, d, nullptr, coef_of<T>(cs));
 }
 
 template <class T>
