@@ -11,9 +11,11 @@ of the whole lattice).  Prints ONE JSON line (rank 0).
             measured HBM copy bandwidth: algorithmic bytes = every population
             read once and written once (FP32: 28 x 4 = 112 B per node-step).
   e2e       same metric through the public API from host memory: the initial
-            state is loaded from a host checkpoint (H2D), every step is
-            followed by a Nusselt read-back (D2H), the final state is saved to
-            host (D2H); host wall clock.
+            state is loaded from a host checkpoint (H2D), the Nusselt numbers
+            of every step are written to pinned host memory (D2H, one
+            lbm_step_nusselt call), the final state is saved to host (D2H);
+            host wall clock.  per_step_calls: the same job with one lbm_step
+            and one lbm_nusselt_async call per step.
   cpu_baseline  the FP64 CPU oracle, as it stands, on the host cores, on a
             bounded number of steps of the same lattice.
   variants  FP64 and FP16-storage throughput of the same lattice, and the mean
@@ -239,10 +241,13 @@ def device_leg(n, precision, steps, warmup, world=1, gpu_index=0, sample_clocks=
 
 
 def e2e_leg(n, precision, steps):
-    """Public API from host memory: load a host checkpoint, step with a
-    Nusselt read-back after every step (lbm_nusselt_async: the kernel writes
-    into pinned host memory, the host waits once at the end), save the final
-    state to host.  One short untimed pass first (first use of the buffers)."""
+    """Public API from host memory: load a host checkpoint, run the steps
+    with the Nusselt numbers of every step written into pinned host memory
+    (lbm_step_nusselt: the step kernel keeps the wall columns' temperatures,
+    a small kernel reduces them; the host waits once at the end), save the
+    final state to host.  The same job with one lbm_step and one
+    lbm_nusselt_async call per step is reported beside it.  One short
+    untimed pass of each first (first use of the buffers)."""
     import torch
 
     from paper_1308_2071_gb300 import Cavity
@@ -261,30 +266,43 @@ def e2e_leg(n, precision, steps):
 
     lib = _lib.load()
     cav = Cavity(n, n, **kw)
+    cav.tune(TUNE_CACHE)  # the launch shape the device leg uses (cached); the load below sets the state
     out = torch.empty(len(pinned), dtype=torch.uint8, pin_memory=True)
     nus = torch.empty((steps, 2), dtype=torch.float64, pin_memory=True)
     base = nus.data_ptr()
 
-    def job(nsteps):
+    def job(nsteps, per_call):
         t0 = time.perf_counter()
         _lib.check(lib.lbm_load(cav.handle, C.c_void_p(pinned.data_ptr()), len(pinned)), cav.handle)  # waits
         t_load = time.perf_counter()
-        for k in range(nsteps):
-            cav.step(1)
-            cav.nusselt_async(base + 16 * k)
+        if per_call:
+            for k in range(nsteps):
+                cav.step(1)
+                cav.nusselt_async(base + 16 * k)
+        else:
+            cav.step_nusselt(nsteps, out=nus)
+        cav.stream.synchronize()  # (the save below would wait here anyway)
+        t_steps = time.perf_counter()
         _lib.check(lib.lbm_save(cav.handle, C.c_void_p(out.data_ptr()), len(out)), cav.handle)  # waits
-        return t0, t_load, time.perf_counter()
+        return t0, t_load, t_steps, time.perf_counter()
 
-    job(8)  # warm-up: first use of the pinned buffers and of the launch path
-    torch.cuda.synchronize()
-    t0, t_load, t1 = job(steps)
-    last = cav.nusselt()
-    assert float(nus[-1, 0]) == last[0], "asynchronous read-back disagrees with lbm_nusselt"
+    res = {}
+    for per_call in (False, True):
+        job(8, per_call)  # warm-up: first use of the pinned buffers and of the launch path
+        torch.cuda.synchronize()
+        nus.zero_()
+        t0, t_load, t_steps, t1 = job(steps, per_call)
+        last = cav.nusselt()
+        assert (float(nus[-1, 0]), float(nus[-1, 1])) == last, "read-back disagrees with lbm_nusselt"
+        res[per_call] = (n * n * steps / (t1 - t0) / 1e6, t1 - t0, t_load - t0, t1 - t_steps)
     cav.close()
-    mlups = n * n * steps / (t1 - t0) / 1e6
+    mlups, secs, load, save = res[False]
     return dict(value=round(mlups, 2), unit="MLUPS", h2d_bytes_per_step=int(len(pinned) / steps),
                 d2h_bytes_per_step=int((len(out) + 16 * steps) / steps), steps=steps,
-                seconds=round(t1 - t0, 4), load_seconds=round(t_load - t0, 4))
+                seconds=round(secs, 4), load_seconds=round(load, 4), save_seconds=round(save, 4),
+                api="lbm_step_nusselt",
+                per_step_calls=dict(value=round(res[True][0], 2), seconds=round(res[True][1], 4),
+                                    api="lbm_step + lbm_nusselt_async per step"))
 
 
 def long_run_leg(n=1024, steps=50000):

@@ -153,6 +153,21 @@ int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void
  * result of every step without stalling.  Errors: LBM_ERR_ARG (NULL), LBM_ERR_CUDA. */
 int lbm_nusselt_async(lbm_handle h, double* out2);
 
+/* Advances nsteps time steps, as lbm_step (the same lattice, bit for bit),
+ * and after step k (0-based) writes the mean Nusselt numbers (Eq. 38) of the
+ * walls x = 0 and x = nx - 1 of the new state to out[2k] and out[2k + 1]: the
+ * values lbm_nusselt would return there, bit for bit.  Each step stores the
+ * temperatures of the five node columns next to each wall as it computes
+ * them (10 doubles per row, double-buffered in the handle), so nothing is
+ * pulled twice; a small kernel reduces them on a second, high-priority
+ * stream of the handle (created on first use) while the next step runs.
+ * out: 2 * nsteps doubles in device memory or page-locked host memory,
+ * caller-owned, written by the GPU directly.  Asynchronous on the handle's
+ * stream: the values are complete once the stream reaches this point.
+ * Errors: LBM_ERR_ARG (NULL handle or out, nsteps < 0, out in pageable host
+ * memory or not aligned for double), LBM_ERR_CUDA. */
+int lbm_step_nusselt(lbm_handle h, long nsteps, double* out);
+
 /* Discrete adjoint (no counterpart in the paper, which has no gradient).
  * Resets the handle to its initial state, runs nsteps steps forward keeping
  * one lattice every ckpt_every steps, evaluates J = mean Nu of the hot wall

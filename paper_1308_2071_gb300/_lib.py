@@ -57,6 +57,7 @@ SIGNATURES = [
     ("lbm_field_extrema", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     ("lbm_nusselt_async", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("lbm_step_nusselt", C.c_int, [C.c_void_p, C.c_long, C.c_void_p]),
     ("lbm_nusselt", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lbm_read_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_checkpoint_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),

@@ -43,6 +43,10 @@ struct lbm_handle_s {
     int* status_dev = nullptr;
     unsigned* nu_counter = nullptr;  // block counter of the row-parallel Nusselt kernel
     double* nu_dev = nullptr;        // its two results
+    double* wall_cols = nullptr;     // two halves of kObsCols temperatures per row, written by observing steps
+    cudaStream_t nu_stream = nullptr;  // lbm_step_nusselt's reductions, beside the next step
+    cudaEvent_t nu_step[2] = {nullptr, nullptr};  // observing step done, per half of wall_cols
+    cudaEvent_t nu_red[2] = {nullptr, nullptr};   // its reduction done
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphExec_t steady_exec = nullptr;
     long steady_key[4] = {0, 0, 0, 0};  // K, parity, max_checks, tol bits
@@ -208,6 +212,12 @@ void free_handle(lbm_handle h) {
     if (h->status_dev) cudaFree(h->status_dev);
     if (h->nu_counter) cudaFree(h->nu_counter);
     if (h->nu_dev) cudaFree(h->nu_dev);
+    if (h->wall_cols) cudaFree(h->wall_cols);
+    for (int b = 0; b < 2; ++b) {
+        if (h->nu_step[b]) cudaEventDestroy(h->nu_step[b]);
+        if (h->nu_red[b]) cudaEventDestroy(h->nu_red[b]);
+    }
+    if (h->nu_stream) cudaStreamDestroy(h->nu_stream);
     if (h->obs_host) cudaFreeHost(h->obs_host);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
@@ -399,6 +409,7 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     CKI(cudaMalloc(&h->nu_counter, sizeof(unsigned)));
     CKI(cudaMemsetAsync(h->nu_counter, 0, sizeof(unsigned), h->stream));
     CKI(cudaMalloc(&h->nu_dev, 2 * sizeof(double)));
+    CKI(cudaMalloc(&h->wall_cols, sizeof(double) * 2 * kObsCols * (size_t)p->ny));
     CKI(cudaMallocHost(&h->obs_host, sizeof(double) * 8));
     const size_t rsz = p->precision == LBM_F64 ? 8 : 4;
     CKI(cudaMalloc(&h->snap, rsz * 2 * (size_t)p->nx * p->ny));
@@ -597,6 +608,22 @@ int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void
 }
 
 namespace {
+// The address a kernel writes to for p: p itself for device and managed
+// memory, the mapped device address for page-locked host memory, nullptr for
+// pageable host memory or a pointer not aligned for doubles.
+double* device_writable(double* p) {
+    if ((uintptr_t)p % alignof(double) != 0) return nullptr;
+    cudaPointerAttributes a;
+    memset(&a, 0, sizeof a);
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return (double*)a.devicePointer;
+    return nullptr;
+}
+
 // out: where the kernel writes (nu_hot, nu_cold); device-accessible memory
 int enqueue_nusselt(lbm_handle h, double* out) {
     if (4 * kReduceBlocks < 2 * ((h->p.ny + 31) / 32)) return fail(h, LBM_ERR_ARG, "too many rows for the reduction");
@@ -633,19 +660,65 @@ int lbm_nusselt_async(lbm_handle h, double* out2) {
     if (!out2) return fail(h, LBM_ERR_ARG, "out2 is NULL");
     // device memory and mapped (pinned) host memory: the kernel writes there
     // itself; other host memory gets a copy
-    cudaPointerAttributes a;
-    memset(&a, 0, sizeof a);
-    if (cudaPointerGetAttributes(&a, out2) != cudaSuccess) {
-        (void)cudaGetLastError();
-        a.type = cudaMemoryTypeUnregistered;
-    }
-    double* direct = nullptr;
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) direct = out2;
-    else if (a.type == cudaMemoryTypeHost && a.devicePointer) direct = (double*)a.devicePointer;
-    if ((uintptr_t)out2 % alignof(double) != 0) direct = nullptr;
+    double* direct = device_writable(out2);
     int rc = enqueue_nusselt(h, direct ? direct : h->nu_dev);
     if (rc != LBM_OK) return rc;
     if (!direct) CK(h, cudaMemcpyAsync(out2, h->nu_dev, sizeof(double) * 2, cudaMemcpyDefault, h->stream));
+    return LBM_OK;
+}
+
+int lbm_step_nusselt(lbm_handle h, long nsteps, double* out) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    if (4 * kReduceBlocks < 2 * ((h->p.ny + 31) / 32)) return fail(h, LBM_ERR_ARG, "too many rows for the reduction");
+    double* dev = device_writable(out);
+    if (!dev) return fail(h, LBM_ERR_ARG, "out must be device memory or page-locked host memory, aligned for double");
+    if (!h->nu_stream) {
+        // the reductions take few blocks: the highest priority lets them in
+        // while the next step's blocks are still being dispatched
+        int least = 0, greatest = 0;
+        CK(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(h, cudaStreamCreateWithPriority(&h->nu_stream, cudaStreamNonBlocking, greatest));
+        for (int b = 0; b < 2; ++b) {
+            CK(h, cudaEventCreateWithFlags(&h->nu_step[b], cudaEventDisableTiming));
+            CK(h, cudaEventCreateWithFlags(&h->nu_red[b], cudaEventDisableTiming));
+        }
+    }
+    ObserveLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.precision = h->precision;
+    L.gm = h->gm;
+    L.partials = h->partials;
+    L.L = h->dv.L;
+    L.dT = h->dv.dT;
+    L.status = h->status_dev;
+    L.counter = h->nu_counter;
+    L.stream = h->nu_stream;
+    // step k writes half k & 1 of wall_cols; its reduction runs on nu_stream
+    // beside step k + 1 (which writes the other half), and step k + 2 waits
+    // for it before rewriting the half
+    for (long k = 0; k < nsteps; ++k) {
+        const int b = (int)(k & 1);
+        double* cols = h->wall_cols + (size_t)b * kObsCols * h->p.ny;
+        if (k >= 2) CK(h, cudaStreamWaitEvent(h->stream, h->nu_red[b], 0));
+        StepLaunch Ls = step_launch(h, h->cur, h->stream);
+        Ls.obs = cols;
+        CK(h, launch_step(Ls, h->coef));
+        h->cur ^= 1;
+        h->t += 1;
+        CK(h, cudaEventRecord(h->nu_step[b], h->stream));
+        CK(h, cudaStreamWaitEvent(h->nu_stream, h->nu_step[b], 0));
+        L.prev = h->buf[h->cur ^ 1];
+        L.obs = cols;
+        L.out = dev + 2 * k;
+        CK(h, launch_nusselt(L, h->coef));
+        CK(h, cudaEventRecord(h->nu_red[b], h->nu_stream));
+    }
+    // the caller's stream reaches this point once the last reduction is done
+    // (the reductions run in order on nu_stream)
+    CK(h, cudaStreamWaitEvent(h->stream, h->nu_red[(nsteps - 1) & 1], 0));
     return LBM_OK;
 }
 

@@ -585,11 +585,38 @@ __device__ __forceinline__ void frame_out(const Coef<typename T::R>& c, const Ge
     Conv<typename T::SG, R, T::cg>::st(dst.t + off, Fn);
 }
 
-// One node of the step: pull (or wall rule), collide, store.
-template <class T, bool FIELD>
+// ---- wall-column temperatures -------------------------------------------------------
+
+// The Nusselt number (Eq. 38) reads T at the five node columns next to each
+// vertical wall.  An observing step stores T - T0 of those nodes of the
+// post-stream state as it computes them: obs[kObsCols y + k] holds node
+// x = k (k < 5) and node x = nx - 1 - (k - 5) (k >= 5), in FP64, the value
+// node_dT reports for a node off the walls (framed storage: frame and local
+// part added in FP64).  A node of a narrow lattice may fill two slots.
+constexpr int kObsCols = 10;
+
+__device__ __forceinline__ void obs_put(const Geom& gm, double* obs, int x, int y, double v) {
+    if (x < 5) obs[kObsCols * y + x] = v;
+    if (x >= gm.nx - 5) obs[kObsCols * y + 5 + (gm.nx - 1 - x)] = v;
+}
+
+template <class T>
+__device__ __forceinline__ double obs_value(const Macro<typename T::R>& m) {
+    if constexpr (Framed<T>::value)
+        return (double)m.F + (double)m.dTl;
+    else
+        return (double)m.dT;
+}
+
+// One node of the step: pull (or wall rule), collide, store; OBS: also the
+// node's temperature into obs when it lies in a wall column.  That store
+// comes after all arithmetic: a branch between the macroscopic values and
+// the collision would change where the compiler fuses multiply-adds, and
+// with it the rounding of the lattice.
+template <class T, bool FIELD, bool OBS = false>
 __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
                                             const Dst<T>& dst, const typename T::P* phi, int x, int y,
-                                            int* status) {
+                                            int* status, double* obs = nullptr) {
     using R = typename T::R;
     R d[9], h[5];
     Drag<R> dr;
@@ -602,16 +629,18 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
 #pragma unroll
     for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+    if constexpr (OBS) obs_put(gm, obs, x, y, obs_value<T>(mc));
 }
 
 // Two fluid nodes from their pulled values in one pass of F2 arithmetic (FP32
 // arithmetic types only): about half the arithmetic instructions of two nodes.
-template <class T>
+template <class T, bool OBS = false>
 __device__ __forceinline__ void collide_fluid_pair_x2(const Coef<float>& c, const Geom& gm, const Dst<T>& dst,
                                                       const float (&a0)[9], const float (&b0)[5],
                                                       const float (&a1)[9], const float (&b1)[5],
                                                       const Drag<float>& r0, const Drag<float>& r1, int off0,
-                                                      int off1, int* status) {
+                                                      int off1, int* status, int x0 = 0, int y0 = 0, int x1 = 0,
+                                                      int y1 = 0, double* obs = nullptr) {
     Drag<F2> dr;
     dr.phi = F2(r0.phi, r1.phi);
     dr.iphi = F2(r0.iphi, r1.iphi);
@@ -635,33 +664,39 @@ __device__ __forceinline__ void collide_fluid_pair_x2(const Coef<float>& c, cons
         Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x);
         Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off1, h[j].v.y);
     }
+    if constexpr (OBS) {
+        // lane-wise IEEE sums: the same values as the scalar path
+        obs_put(gm, obs, x0, y0, (double)m.dT.v.x);
+        obs_put(gm, obs, x1, y1, (double)m.dT.v.y);
+    }
 }
 
-template <class T, bool FIELD>
+template <class T, bool FIELD, bool OBS = false>
 __device__ __forceinline__ void update_fluid_pair_x2(const Coef<float>& c, const Geom& gm, const Src<T>& src,
-                                                     const Dst<T>& dst, const typename T::P* phi, int off0, int off1,
-                                                     int* status) {
+                                                     const Dst<T>& dst, const typename T::P* phi, int x0, int y0,
+                                                     int x1, int y1, int* status, double* obs = nullptr) {
+    const int off0 = y0 * gm.pitch + x0, off1 = y1 * gm.pitch + x1;
     float a0[9], b0[5], a1[9], b1[5];
     pull<T>(src, gm, off0, a0, b0);
     pull<T>(src, gm, off1, a1, b1);
     const Drag<float> r0 = drag_at<float, FIELD, typename T::P>(c, phi, off0);
     const Drag<float> r1 = drag_at<float, FIELD, typename T::P>(c, phi, off1);
-    collide_fluid_pair_x2<T>(c, gm, dst, a0, b0, a1, b1, r0, r1, off0, off1, status);
+    collide_fluid_pair_x2<T, OBS>(c, gm, dst, a0, b0, a1, b1, r0, r1, off0, off1, status, x0, y0, x1, y1, obs);
 }
 
 // Two nodes at once: when both are fluid nodes all 28 loads are issued before
 // any arithmetic (twice the bytes in flight of one node per thread); nodes
 // outside the lattice (valid = false) or on walls take the one-node path.
-template <class T, bool FIELD>
+template <class T, bool FIELD, bool OBS = false>
 __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
                                             const Dst<T>& dst, const typename T::P* phi, int x0, int y0,
-                                            bool v0, int x1, int y1, bool v1, int* status) {
+                                            bool v0, int x1, int y1, bool v1, int* status, double* obs = nullptr) {
     using R = typename T::R;
     const bool f0 = v0 && x0 > 0 && x0 < gm.nx - 1 && y0 > 0 && y0 < gm.ny - 1;
     const bool f1 = v1 && x1 > 0 && x1 < gm.nx - 1 && y1 > 0 && y1 < gm.ny - 1;
     if constexpr (Paired<T>::value) {
         if (f0 && f1) {
-            update_fluid_pair_x2<T, FIELD>(c, gm, src, dst, phi, y0 * gm.pitch + x0, y1 * gm.pitch + x1, status);
+            update_fluid_pair_x2<T, FIELD, OBS>(c, gm, src, dst, phi, x0, y0, x1, y1, status, obs);
             return;
         }
     }
@@ -697,10 +732,14 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
             Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
             Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
         }
+        if constexpr (OBS) {
+            obs_put(gm, obs, x0, y0, obs_value<T>(m0));
+            obs_put(gm, obs, x1, y1, obs_value<T>(m1));
+        }
         return;
     }
-    if (v0) update_node<T, FIELD>(c, gm, src, dst, phi, x0, y0, status);
-    if (v1) update_node<T, FIELD>(c, gm, src, dst, phi, x1, y1, status);
+    if (v0) update_node<T, FIELD, OBS>(c, gm, src, dst, phi, x0, y0, status, obs);
+    if (v1) update_node<T, FIELD, OBS>(c, gm, src, dst, phi, x1, y1, status, obs);
 }
 
 // T - T0 of the post-stream state at node (x, y), pulled from B_{n-1}
@@ -737,6 +776,31 @@ __device__ __forceinline__ double node_dT(const Coef<typename T::R>& c, const Ge
         }
         return (double)dTf;
     }
+}
+
+// node_dT of node (x, y), x = k (k < 5) or nx - 1 - (k - 5), from the wall
+// columns an observing step stored (obs_put): the stored value off the walls;
+// on the walls the wall rule's temperature, imposed on the vertical walls and,
+// on the adiabatic rows, taken from the stored rows next to them in the
+// arithmetic node_dT uses, so both give the same bits.
+template <class T>
+__device__ __forceinline__ double obs_dT(const Coef<typename T::R>& c, const Geom& gm, const double* obs, int k,
+                                         int y) {
+    using R = typename T::R;
+    const int x = k < 5 ? k : gm.nx - 1 - (k - 5);
+    const Normal nr = normal_of(gm, x, y);
+    if (nr.dx == 0 && nr.dy == 0) return obs[kObsCols * y + k];
+    if (gm.thermal_bc == 1) return (double)c.dTc;
+    if (nr.dx != 0) return (double)(x == 0 ? c.dTh : c.dTc);
+    const double tf = obs[kObsCols * (y + nr.dy) + k];
+    if (gm.adi_order == 2) {
+        const double tff = obs[kObsCols * (y + 2 * nr.dy) + k];
+        if constexpr (Framed<T>::value)
+            return (4.0 * tf - tff) / 3.0;
+        else
+            return (double)((R(4) * R(tf) - R(tff)) * R(1.0 / 3.0));
+    }
+    return tf;
 }
 
 // Block-wide reduction of four doubles: max, max, sum, sum (result in thread 0).

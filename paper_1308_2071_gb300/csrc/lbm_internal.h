@@ -54,6 +54,7 @@ struct StepLaunch {
     int* status;
     cudaStream_t stream;
     bool pdl = false;  // launch as a programmatic dependent of the previous step
+    double* obs = nullptr;  // observing step: wall-column temperatures (kObsCols per row)
 };
 
 struct ObserveLaunch {
@@ -70,6 +71,7 @@ struct ObserveLaunch {
     const int* status;
     double* out;            // 7 doubles
     unsigned* counter = nullptr;  // launch_nusselt: zero-initialised block counter
+    const double* obs = nullptr;  // launch_nusselt: read the wall columns an observing step stored
     cudaStream_t stream;
 };
 

@@ -20,14 +20,18 @@ namespace lbm {
 // Without that launch attribute the wait returns at once.
 __device__ __forceinline__ void wait_for_previous_step() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <class T, bool FIELD>
+// OBS: an observing step, which also stores the temperatures of the node
+// columns next to the vertical walls into obs (obs_put) for the Nusselt
+// number of the new state; otherwise obs is unused.
+template <class T, bool FIELD, bool OBS>
 __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
-                                              Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+                                              Geom gm, Coef<typename T::R> c, int* __restrict__ status,
+                                              double* __restrict__ obs) {
     wait_for_previous_step();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= gm.nx || y >= gm.ny) return;
-    update_node<T, FIELD>(c, gm, src, dst, phi, x, y, status);
+    update_node<T, FIELD, OBS>(c, gm, src, dst, phi, x, y, status, obs);
 }
 
 // Two nodes per thread, (x, y) and (x, y + blockDim.y): when both are fluid
@@ -39,16 +43,16 @@ __global__ void __launch_bounds__(256) k_step(Src<T> src, Dst<T> dst, const type
 // per SM), which measured faster than the unconstrained 68-80 registers at
 // every size and storage type: more warps keep more loads in flight.  FP64
 // would spill under that limit.
-template <class T, bool FIELD>
+template <class T, bool FIELD, bool OBS>
 __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 4 : 1)
-    k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi,
-                                               Geom gm, Coef<typename T::R> c, int* __restrict__ status) {
+    k_step2(Src<T> src, Dst<T> dst, const typename T::P* __restrict__ phi, Geom gm, Coef<typename T::R> c,
+            int* __restrict__ status, double* __restrict__ obs) {
     wait_for_previous_step();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y0 = blockIdx.y * (2 * blockDim.y) + threadIdx.y;
     const int y1 = y0 + blockDim.y;
     if (x >= gm.nx || y0 >= gm.ny) return;
-    update_pair<T, FIELD>(c, gm, src, dst, phi, x, y0, true, x, y1, y1 < gm.ny, status);
+    update_pair<T, FIELD, OBS>(c, gm, src, dst, phi, x, y0, true, x, y1, y1 < gm.ny, status, obs);
 }
 
 // ---- observables ------------------------------------------------------------------
@@ -137,11 +141,14 @@ __global__ void __launch_bounds__(1024) k_finish(Src<T> prev, Geom gm, Coef<type
 // Row-parallel mean Nusselt numbers (Eq. 38): one thread per wall row in
 // one-warp blocks (so the rows' scattered loads spread over many SMs), warp
 // sums into partials; the last block to finish folds the partials in a fixed
-// order (deterministic), writes out[0..1] and re-arms the counter.
-template <class T>
-__global__ void __launch_bounds__(32) k_nusselt_rows(Src<T> prev, Geom gm, Coef<typename T::R> c, double L,
-                                                     double dT, double* __restrict__ partials,
-                                                     unsigned* __restrict__ counter, double* __restrict__ out) {
+// order (deterministic), writes out[0..1] and re-arms the counter.  OBS: the
+// temperatures come from the wall columns the step before stored (obs_dT),
+// else they are pulled from B_{n-1} (node_dT); both give the same values.
+template <class T, bool OBS>
+__global__ void __launch_bounds__(32) k_nusselt_rows(Src<T> prev, const double* __restrict__ obs, Geom gm,
+                                                     Coef<typename T::R> c, double L, double dT,
+                                                     double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                     double* __restrict__ out) {
     __shared__ bool last;
     double a = 0.0, b = 0.0;
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,8 +156,13 @@ __global__ void __launch_bounds__(32) k_nusselt_rows(Src<T> prev, Geom gm, Coef<
         double tl[5], tr[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
-            tr[k] = (double)node_dT<T>(c, gm, prev, gm.nx - 1 - k, y);
+            if constexpr (OBS) {
+                tl[k] = obs_dT<T>(c, gm, obs, k, y);
+                tr[k] = obs_dT<T>(c, gm, obs, 5 + k, y);
+            } else {
+                tl[k] = (double)node_dT<T>(c, gm, prev, k, y);
+                tr[k] = (double)node_dT<T>(c, gm, prev, gm.nx - 1 - k, y);
+            }
         }
         const double dl = (-25.0 * tl[0] + 48.0 * tl[1] - 36.0 * tl[2] + 16.0 * tl[3] - 3.0 * tl[4]) / 12.0;
         const double dr = (25.0 * tr[0] - 48.0 * tr[1] + 36.0 * tr[2] - 16.0 * tr[3] + 3.0 * tr[4]) / 12.0;
@@ -247,23 +259,27 @@ static cudaError_t launch_one_step(K k, dim3 grd, dim3 blk, const StepLaunch& L,
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = L.pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k, s, d, phi, L.gm, c, L.status);
+    return cudaLaunchKernelEx(&cfg, k, s, d, phi, L.gm, c, L.status, L.obs);
+}
+
+template <class T, bool FIELD, bool OBS>
+static cudaError_t launch_step_k(const StepLaunch& L, const CoefSet& cs) {
+    dim3 blk(L.bx, L.by);
+    const Src<T> s = src_view<T>(L.src, L.gm.plane);
+    const Dst<T> d = dst_view<T>(L.dst, L.gm.plane);
+    const typename T::P* phi = FIELD ? (const typename T::P*)L.phi : nullptr;
+    if (L.npt == 2) {
+        dim3 grd2((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + 2 * L.by - 1) / (2 * L.by));
+        return launch_one_step<T>(k_step2<T, FIELD, OBS>, grd2, blk, L, s, d, phi, coef_of<T>(cs));
+    }
+    dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
+    return launch_one_step<T>(k_step<T, FIELD, OBS>, grd, blk, L, s, d, phi, coef_of<T>(cs));
 }
 
 template <class T>
 static cudaError_t launch_step_t(const StepLaunch& L, const CoefSet& cs) {
-    dim3 blk(L.bx, L.by);
-    const Src<T> s = src_view<T>(L.src, L.gm.plane);
-    const Dst<T> d = dst_view<T>(L.dst, L.gm.plane);
-    const typename T::P* phi = (const typename T::P*)L.phi;
-    if (L.npt == 2) {
-        dim3 grd2((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + 2 * L.by - 1) / (2 * L.by));
-        if (L.phi) return launch_one_step<T>(k_step2<T, true>, grd2, blk, L, s, d, phi, coef_of<T>(cs));
-        return launch_one_step<T>(k_step2<T, false>, grd2, blk, L, s, d, nullptr, coef_of<T>(cs));
-    }
-    dim3 grd((L.gm.nx + L.bx - 1) / L.bx, (L.gm.ny + L.by - 1) / L.by);
-    if (L.phi) return launch_one_step<T>(k_step<T, true>, grd, blk, L, s, d, phi, coef_of<T>(cs));
-    return launch_one_step<T>(k_step<T, false>, grd, blk, L, s, d, nullptr, coef_of<T>(cs));
+    if (L.obs) return L.phi ? launch_step_k<T, true, true>(L, cs) : launch_step_k<T, false, true>(L, cs);
+    return L.phi ? launch_step_k<T, true, false>(L, cs) : launch_step_k<T, false, false>(L, cs);
 }
 
 template <class T>
@@ -289,8 +305,13 @@ template <class T>
 static cudaError_t launch_nusselt_t(const ObserveLaunch& L, const CoefSet& cs) {
     // partials holds 2 doubles per block; counter is zero between launches
     const int nb = (L.gm.ny + 31) / 32;
-    k_nusselt_rows<T><<<nb, 32, 0, L.stream>>>(src_view<T>(L.prev, L.gm.plane), L.gm, coef_of<T>(cs), L.L, L.dT,
-                                                L.partials, L.counter, L.out);
+    const Src<T> s = src_view<T>(L.prev, L.gm.plane);
+    if (L.obs)
+        k_nusselt_rows<T, true><<<nb, 32, 0, L.stream>>>(s, L.obs, L.gm, coef_of<T>(cs), L.L, L.dT, L.partials,
+                                                         L.counter, L.out);
+    else
+        k_nusselt_rows<T, false><<<nb, 32, 0, L.stream>>>(s, nullptr, L.gm, coef_of<T>(cs), L.L, L.dT, L.partials,
+                                                          L.counter, L.out);
     return cudaGetLastError();
 }
 

@@ -154,6 +154,20 @@ class Cavity:
         out2_ptr (pinned host or device memory) without waiting."""
         L.check(L.load().lbm_nusselt_async(self._h, C.c_void_p(out2_ptr)), self._h)
 
+    def step_nusselt(self, n: int, out=None):
+        """Advances n steps; row k of the (n, 2) FP64 result holds (Nu of the
+        hot wall, Nu of the cold wall) after step k (Eq. 38), as nusselt()
+        would give there.  out: optional float64 tensor of 2n elements on this
+        device or in pinned host memory; written asynchronously (complete once
+        the handle's stream is)."""
+        n = int(n)
+        if out is None:
+            out = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        elif out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < 2 * n:
+            raise ValueError("out must be a contiguous float64 tensor of at least 2n elements")
+        L.check(L.load().lbm_step_nusselt(self._h, n, C.c_void_p(out.data_ptr())), self._h)
+        return out
+
     def read_state(self):
         """Full FP64 post-stream populations f (9, ny, nx) and g (5, ny, nx)."""
         f = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)

@@ -111,6 +111,7 @@ def test_null_handles_are_errors_not_crashes(lib):
     from paper_1308_2071_gb300 import _lib
 
     assert lib.lbm_step(None, 1) == _lib.LBM_ERR_ARG
+    assert lib.lbm_step_nusselt(None, 1, None) == _lib.LBM_ERR_ARG
     assert lib.lbm_destroy(None) == _lib.LBM_OK
     assert lib.lbm_init(None, None, None) == _lib.LBM_ERR_ARG
 

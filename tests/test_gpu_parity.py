@@ -412,6 +412,86 @@ def test_nusselt_readback_matches_oracle(precision, tol, shape, nthreads):
     cav.close()
 
 
+# ---- Nusselt numbers of every step from the step kernel (lbm_step_nusselt) ------------
+
+# name: (nx, ny, precision, keyword arguments); "field" adds a seeded porosity field
+STEP_NU_CASES = {
+    "f64": (40, 31, "f64", {}),
+    "f32_two_nodes": (96, 70, "f32", dict(nodes_per_thread=2, block_x=32, block_y=4)),
+    "f32_one_node": (96, 70, "f32", dict(nodes_per_thread=1, block_x=64, block_y=2)),
+    "f16_paired": (96, 70, "f16", dict(nodes_per_thread=2, block_x=64, block_y=2)),
+    "f32t": (96, 70, "f32t", {}),
+    "f32t_adiabatic_order2": (40, 36, "f32t", dict(adiabatic_order=2)),
+    "f32_adiabatic_order2": (40, 36, "f32", dict(adiabatic_order=2)),
+    "f64_field": (48, 40, "f64", "field"),
+    "f32_field": (48, 40, "f32", "field"),
+    "narrow": (7, 9, "f32", {}),  # the column sets of both walls overlap
+    "cooled": (48, 48, "f64", dict(Ra=0.0, Da=1e-2, phi=1.0, Pr=7.0, RaI=6.4e5, thermal_bc=1, forchheimer=0)),
+}
+
+
+@pytest.mark.parametrize("case", list(STEP_NU_CASES))
+def test_step_nusselt_equals_step_then_nusselt(case):
+    """Every step's Nusselt numbers from the wall columns the observing step
+    stores equal lbm_nusselt after lbm_step bit for bit, and the lattice is
+    the same, in device and in pinned host output memory."""
+    import torch
+
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    nx, ny, precision, kw = STEP_NU_CASES[case]
+    base = dict(Ra=1e5, Da=1e-2, phi=0.6, precision=precision)
+    if kw == "field":
+        phi = perturbed_porosity(ny, nx, phi_bar=0.6, amplitude=0.1, corr_len=6.0, seed=5)
+        kw = dict(phi_field=torch.from_numpy(phi).cuda())
+    base.update(kw)
+    a, b = cavity(nx, ny, **base), cavity(nx, ny, **base)
+    n1, n2 = 40, 17
+    ref = np.array([a.step(1).nusselt() for _ in range(n1 + n2)])
+    got_dev = b.step_nusselt(n1)
+    host = torch.zeros((n2, 2), dtype=torch.float64, pin_memory=True)
+    b.step_nusselt(n2, out=host)
+    b.stream.synchronize()
+    got = np.concatenate([got_dev.cpu().numpy(), host.numpy()])
+    assert np.array_equal(got, ref), np.abs(got - ref).max()
+    assert np.isfinite(ref).all() and a.query()[0] == b.query()[0] == n1 + n2
+    assert bytes(a.save()) == bytes(b.save())
+    assert b.nusselt() == tuple(ref[-1])
+    a.close()
+    b.close()
+
+
+def test_step_nusselt_matches_oracle_series(nthreads):
+    """Config 1 lattice: the per-step Nusselt series against the oracle's at
+    the steps it is sampled on."""
+    o = Oracle(derive(64, 64, Ra=1e4, Da=1e-2, phi=0.6))
+    cav = cavity(64, 64, Ra=1e4, Da=1e-2, phi=0.6, precision="f64")
+    series = cav.step_nusselt(300).cpu().numpy()
+    for t in (1, 2, 50, 299, 300):
+        o.step(t - o.t, threads=nthreads)
+        onh, onc = o.nusselt()
+        nh, nc = series[t - 1]
+        assert abs(nh - onh) <= 1e-11 * abs(onh) and abs(nc - onc) <= 1e-11 * abs(onc), (t, nh, onh, nc, onc)
+    cav.close()
+
+
+def test_step_nusselt_rejects_pageable_output_and_bad_arguments():
+    import ctypes as C
+
+    from paper_1308_2071_gb300 import _lib
+
+    lib = _lib.load()
+    cav = cavity(32, 32, Ra=1e4, Da=1e-2, phi=0.6)
+    pageable = (C.c_double * 8)()
+    assert lib.lbm_step_nusselt(cav.handle, 4, C.cast(pageable, C.c_void_p)) == _lib.LBM_ERR_ARG
+    assert "page-locked" in lib.lbm_last_error(cav.handle).decode()
+    assert lib.lbm_step_nusselt(cav.handle, 4, None) == _lib.LBM_ERR_ARG
+    assert lib.lbm_step_nusselt(cav.handle, -1, None) == _lib.LBM_ERR_ARG
+    assert lib.lbm_step_nusselt(cav.handle, 0, None) == _lib.LBM_OK
+    assert cav.query()[0] == 0  # nothing ran
+    cav.close()
+
+
 # ---- config 2 at 1024^2, a long run -----------------------------------------------------
 
 @pytest.fixture(scope="module")
