@@ -89,15 +89,59 @@ __device__ __forceinline__ void tile_node(const Tile& tl, int lg_tw, int j, int 
     }
 }
 
-// One launch runs `nsteps` steps of every cavity.  Buffer parity `par` of
-// every cavity holds B_n on entry.
+// The coefficients that differ between the cavities of a sweep follow from
+// Ra, Da, the porosity and the size: the viscous and thermal relaxation
+// rates (Eq. 20, 31), g beta and the drag coefficients (Eq. 4-5).  cu with
+// those fields taken from v.
+template <class R>
+__host__ __device__ __forceinline__ Coef<R> with_cavity_rates(const Coef<R>& cu, const Coef<R>& v) {
+    Coef<R> c = cu;
+    c.s[7] = v.s[7];
+    c.s[8] = v.s[8];
+    c.hs[7] = v.hs[7];
+    c.hs[8] = v.hs[8];
+    c.z[1] = v.z[1];
+    c.z[2] = v.z[2];
+    c.hz[1] = v.hz[1];
+    c.hz[2] = v.hz[2];
+    c.gbeta = v.gbeta;
+    c.phi = v.phi;
+    c.c_lin = v.c_lin;
+    c.c_quad = v.c_quad;
+    c.a_lin = v.a_lin;
+    c.a_quad = v.a_quad;
+    return c;
+}
+
+// One tile of one step: tiles hold blockDim.x * NPT nodes.
 template <class T, int NPT>
+__device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
+                                            const Dst<T>& dst, const Tile& tl, int lg_tw, int* status) {
+    if constexpr (NPT == 2) {
+        int x0, y0, x1, y1;
+        tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
+        tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
+        update_pair<T, false>(c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
+                              x1 < gm.nx && y1 < gm.ny, status);
+    } else {
+        int x, y;
+        tile_node(tl, lg_tw, threadIdx.x, gm.nx, x, y);
+        if (x < gm.nx && y < gm.ny) update_node<T, false>(c, gm, src, dst, nullptr, x, y, status);
+    }
+}
+
+// One launch runs `nsteps` steps of every cavity.  Buffer parity `par` of
+// every cavity holds B_n on entry.  SPLIT (FP32 arithmetic, every cavity's
+// other coefficients equal to cu's): the per-cavity rates come from the
+// descriptor in shared memory and every other coefficient from the kernel
+// parameter cu, which instructions read from the constant bank; without
+// SPLIT all come from the descriptor (about 45 values per tile in registers).
+template <class T, int NPT, bool SPLIT>
 __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 4 : 3) : 2)
     k_batch(const CavDesc<typename T::R>* __restrict__ cavs, const Tile* __restrict__ tiles, int ntiles, int lg_tw,
-            int dyn, int* __restrict__ tile_ctr,
-                                               long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
-                                               long long wait_limit, int* __restrict__ status,
-                                               int* __restrict__ timeout_flag) {
+            int dyn, int* __restrict__ tile_ctr, long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
+            long long wait_limit, int* __restrict__ status, int* __restrict__ timeout_flag,
+            const Coef<typename T::R> cu) {
     using R = typename T::R;
     __shared__ CavDesc<R> cd;
     __shared__ int chunk_sh;
@@ -177,18 +221,10 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
                 const Geom gm = cd.gm;
                 const Src<T> src = src_view<T>(cd.buf[ps], gm.plane);
                 const Dst<T> dst = dst_view<T>(cd.buf[ps ^ 1], gm.plane);
-                if constexpr (NPT == 2) {
-                    int x0, y0, x1, y1;
-                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
-                    tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
-                    update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
-                                          x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
-                } else {
-                    int x, y;
-                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x, y);
-                    if (x < gm.nx && y < gm.ny)
-                        update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
-                }
+                if constexpr (SPLIT)
+                    tile_update<T, NPT>(with_cavity_rates(cu, cd.c), gm, src, dst, tl, lg_tw, &status[tl.cav]);
+                else
+                    tile_update<T, NPT>(cd.c, gm, src, dst, tl, lg_tw, &status[tl.cav]);
                 // the block's stores happen before this barrier; thread 0's GPU-scope
                 // fence (cumulative) orders them before the count is published
                 __syncthreads();
@@ -233,19 +269,10 @@ __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 
                 const Geom gm = cd.gm;
                 const Src<T> src = src_view<T>(cd.buf[par], gm.plane);
                 const Dst<T> dst = dst_view<T>(cd.buf[par ^ 1], gm.plane);
-                // tiles hold blockDim.x * NPT nodes
-                if constexpr (NPT == 2) {
-                    int x0, y0, x1, y1;
-                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
-                    tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
-                    update_pair<T, false>(cd.c, gm, src, dst, nullptr, x0, y0, x0 < gm.nx && y0 < gm.ny, x1, y1,
-                                          x1 < gm.nx && y1 < gm.ny, &status[tl.cav]);
-                } else {
-                    int x, y;
-                    tile_node(tl, lg_tw, threadIdx.x, gm.nx, x, y);
-                    if (x < gm.nx && y < gm.ny)
-                        update_node<T, false>(cd.c, gm, src, dst, nullptr, x, y, &status[tl.cav]);
-                }
+                if constexpr (SPLIT)
+                    tile_update<T, NPT>(with_cavity_rates(cu, cd.c), gm, src, dst, tl, lg_tw, &status[tl.cav]);
+                else
+                    tile_update<T, NPT>(cd.c, gm, src, dst, tl, lg_tw, &status[tl.cav]);
             }
             if (!dyn) break;
         }
@@ -351,6 +378,7 @@ struct lbm_batch_s {
     int par = 0;  // parity holding B_n
     long t = 0;
     TuneChoice tune;
+    bool split = false;  // k_batch<T, NPT, true>: batch-wide coefficients from the constant bank
     int nblocks = 0;
     long long wait_limit = kDefaultWaitPolls;
     cudaGraphExec_t gexec = nullptr;
@@ -375,14 +403,17 @@ int bfail(lbm_batch b, int code, const std::string& m) {
         if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-template <class T> const void* kernel_ptr(int npt) {
-    return npt == 2 ? (const void*)&k_batch<T, 2> : (const void*)&k_batch<T, 1>;
+template <class T, bool SPLIT> const void* kernel_ptr(int npt) {
+    return npt == 2 ? (const void*)&k_batch<T, 2, SPLIT> : (const void*)&k_batch<T, 1, SPLIT>;
 }
 
-const void* batch_kernel(int precision, int npt) {
-    if (precision == LBM_F64) return kernel_ptr<PrecF64P>(npt);
-    if (precision == LBM_F32_FRAMED) return kernel_ptr<PrecF32TP>(npt);
-    return kernel_ptr<PrecF32P>(npt);
+// FP64 keeps every coefficient in the descriptor: with the split its
+// two-node body spills.
+const void* batch_kernel(int precision, int npt, bool split) {
+    if (precision == LBM_F64) return kernel_ptr<PrecF64P, false>(npt);
+    if (precision == LBM_F32_FRAMED)
+        return split ? kernel_ptr<PrecF32TP, true>(npt) : kernel_ptr<PrecF32TP, false>(npt);
+    return split ? kernel_ptr<PrecF32P, true>(npt) : kernel_ptr<PrecF32P, false>(npt);
 }
 
 int npt_of(const TuneChoice& t) { return tile_nodes(t) == 2 * block_of(t) ? 2 : 1; }
@@ -427,7 +458,7 @@ int grid_size(lbm_batch b, int* nblocks) {
     int dev = 0, nsm = 0, per_sm = 0;
     BCK(b, cudaGetDevice(&dev));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const void* k = batch_kernel(b->precision, npt_of(b->tune));
+    const void* k = batch_kernel(b->precision, npt_of(b->tune), b->split);
     BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block_of(b->tune), 0));
     if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "batched kernel cannot be resident");
     int want = b->tune.blocks_per_sm > 0 ? std::min(b->tune.blocks_per_sm, per_sm) : per_sm;
@@ -459,12 +490,15 @@ int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
     args[10] = &lim;
     args[11] = &b->status;
     args[12] = &b->timeout_flag;
+    Coef<float> cuf = b->coef[0].f;  // the batch-wide coefficients (SPLIT kernels read them)
+    Coef<double> cud = b->coef[0].d;
+    args[13] = b->precision == LBM_F64 ? (void*)&cud : (void*)&cuf;
     cudaError_t ez = cudaMemsetAsync(b->tile_ctr, 0, 2 * sizeof(int), s);
     if (ez == cudaSuccess && b->tune.dyn == 2)  // finished-tile counters of the dataflow mode
         ez = cudaMemsetAsync(b->bar + 2, 0, sizeof(unsigned) * (size_t)b->ncav, s);
     if (ez != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("counter reset: ") + cudaGetErrorString(ez));
     const int npt = npt_of(b->tune);
-    const void* k = batch_kernel(b->precision, npt);
+    const void* k = batch_kernel(b->precision, npt, b->split);
     cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(b->nblocks), dim3(block_of(b->tune)), args, 0, s);
     if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
     return LBM_OK;
@@ -480,6 +514,14 @@ template <class R> int upload_descs(lbm_batch b) {
         if constexpr (sizeof(R) == 8) h[c].c = b->coef[c].d;
         else h[c].c = b->coef[c].f;
     }
+    // the split kernels need every coefficient but the per-cavity rates equal
+    // across the batch, bit for bit
+    bool split = sizeof(R) == 4;
+    for (int c = 1; c < b->ncav && split; ++c) {
+        const Coef<R> x = with_cavity_rates(h[0].c, h[c].c);
+        split = memcmp(&x, &h[c].c, sizeof(Coef<R>)) == 0;
+    }
+    b->split = split;
     if (!b->descs) BCK(b, cudaMalloc(&b->descs, sizeof(CavDesc<R>) * b->ncav));
     BCK(b, cudaMemcpy(b->descs, h.data(), sizeof(CavDesc<R>) * b->ncav, cudaMemcpyHostToDevice));
     return LBM_OK;

@@ -100,6 +100,30 @@ def test_one_node_tiles_are_bit_identical_to_the_single_cavity_kernel(tiles, pre
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["f32", "f32t"])
+def test_cavities_with_their_own_wall_temperatures_are_bit_identical(precision):
+    # wall temperatures that differ between cavities change coefficients that
+    # are otherwise batch-wide: the batch then takes every coefficient from
+    # the cavity's descriptor (the other kernel variant), with the same results
+    from paper_1308_2071_gb300 import Batch, Cavity
+
+    cavs = [dict(cv) for cv in CAVS]
+    cavs[1].update(Th=1.5, Tc=-0.25)
+    cavs[3].update(Th=0.75)
+    b = Batch([dict(cv) for cv in cavs], precision=precision)
+    b.set_tiles(32, 1, 0, 1)
+    b.step(200)
+    for k, cv in enumerate(cavs):
+        extra = {key: cv[key] for key in ("Th", "Tc") if key in cv}
+        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision=precision,
+                   nodes_per_thread=1, **extra)
+        c.step(200)
+        assert np.array_equal(np_(c.read_state()[0]), np_(b.read_state(k)[0])), k
+        assert np.array_equal(np_(c.read_state()[1]), np_(b.read_state(k)[1])), k
+        c.close()
+    b.close()
+
+
 @pytest.mark.parametrize("tiles", [(32, 16), (64, 0), (512, 0)])
 def test_two_node_tiles_agree_with_the_single_cavity_kernel(tiles):
     from paper_1308_2071_gb300 import Batch, Cavity
