@@ -7,7 +7,7 @@ It is written differently from the oracle on purpose:
   inverted with numpy.linalg.inv;
 - equilibria are taken in velocity space (Eq. 13 and Eq. 37 first occurrence)
   and projected, m_eq = M f_eq; the forcing is the Guo-Zhao velocity-space
-  term projected, S = M S~ (the survey of the paper's Section 3.1);
+  term projected, S = M S~ (the form the paper's Section 3.1 reviews);
 - streaming uses np.roll over whole planes;
 - the wall rule is vectorised over each edge.
 """
