@@ -346,6 +346,34 @@ def test_conduction_limit():
     assert abs(nl - 1) < 1e-10 and abs(nr - 1) < 1e-10
 
 
+@pytest.mark.parametrize("profile", ["quadratic", "quartic", "quintic"])
+def test_nusselt_of_polynomial_temperature_profiles(profile):
+    # Eq. 38 on a state whose temperature is T(x) = 1 - x/L + eps q(x) in every
+    # row (fluid at rest, thermal populations at equilibrium), with q = x (L - x),
+    # x^3 (L - x) or x^4 (L - x): the one-sided five-point derivative is exact
+    # up to degree 4, so the first two give Nu from T'(0) and T'(L) exactly; on
+    # the quintic its truncation error is h^4/5 T^(5) = 24 eps (h = 1) at the
+    # hot wall and 24 eps at the cold wall (the -s^5 term of q about x = L).
+    nx, ny = 21, 9
+    L = nx - 1.0
+    lat = derive(nx, ny, Ra=1e4, Da=1e-2, phi=0.6)
+    lat.gbeta = 0.0
+    o = Oracle(lat)
+    f, g0 = o.state()  # rest state
+    x = np.arange(nx, dtype=np.float64)
+    eps, q, nu_hot, nu_cold = {
+        "quadratic": (1e-4, x * (L - x), 1 - 1e-4 * L**2, 1 + 1e-4 * L**2),
+        "quartic": (1e-7, x**3 * (L - x), 1.0, 1 + 1e-7 * L**4),
+        "quintic": (1e-8, x**4 * (L - x), 1 - 24e-8 * L, 1 + 1e-8 * L**5 - 24e-8 * L),
+    }[profile]
+    T = 1.0 - x / L + eps * q
+    wt = g0[:, ny // 2, nx // 2] / lat.T0  # interior rest node: the D2Q5 weights of Eq. 37 (first occurrence)
+    g = wt[:, None, None] * np.broadcast_to(T, (ny, nx))[None, :, :]
+    o.set_state(f, g)  # applies the wall rule: T_h, T_c on the side walls, T_f on the adiabatic rows
+    nl, nr = o.nusselt()
+    assert abs(nl - nu_hot) < 1e-12 and abs(nr - nu_cold) < 1e-12, (nl, nu_hot, nr, nu_cold)
+
+
 def test_derived_parameters_reproduce_the_dimensionless_groups():
     # Section 2 defines Ra, Pr, Da; Eq. 24 and A9 give nu_e and alpha_e from the
     # relaxation times; U = sqrt(g beta dT L) = Ma c_s.  Recover the inputs.
