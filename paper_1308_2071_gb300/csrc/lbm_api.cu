@@ -699,26 +699,45 @@ int lbm_step_nusselt(lbm_handle h, long nsteps, double* out) {
     // step k writes half k & 1 of wall_cols; its reduction runs on nu_stream
     // beside step k + 1 (which writes the other half), and step k + 2 waits
     // for it before rewriting the half
+    cudaError_t e = cudaSuccess;
+    const char* where = "";
     for (long k = 0; k < nsteps; ++k) {
         const int b = (int)(k & 1);
         double* cols = h->wall_cols + (size_t)b * kObsCols * h->p.ny;
-        if (k >= 2) CK(h, cudaStreamWaitEvent(h->stream, h->nu_red[b], 0));
+        if (k >= 2 && (e = cudaStreamWaitEvent(h->stream, h->nu_red[b], 0)) != cudaSuccess) {
+            where = "wait for the reduction two steps back";
+            break;
+        }
         StepLaunch Ls = step_launch(h, h->cur, h->stream);
         Ls.obs = cols;
-        CK(h, launch_step(Ls, h->coef));
+        if ((e = launch_step(Ls, h->coef)) != cudaSuccess) {
+            where = "observing step";
+            break;
+        }
         h->cur ^= 1;
         h->t += 1;
-        CK(h, cudaEventRecord(h->nu_step[b], h->stream));
-        CK(h, cudaStreamWaitEvent(h->nu_stream, h->nu_step[b], 0));
+        if ((e = cudaEventRecord(h->nu_step[b], h->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->nu_stream, h->nu_step[b], 0)) != cudaSuccess) {
+            where = "hand-over to the reduction stream";
+            break;
+        }
         L.prev = h->buf[h->cur ^ 1];
         L.obs = cols;
         L.out = dev + 2 * k;
-        CK(h, launch_nusselt(L, h->coef));
-        CK(h, cudaEventRecord(h->nu_red[b], h->nu_stream));
+        if ((e = launch_nusselt(L, h->coef)) != cudaSuccess ||
+            (e = cudaEventRecord(h->nu_red[b], h->nu_stream)) != cudaSuccess) {
+            where = "wall-column reduction";
+            break;
+        }
     }
     // the caller's stream reaches this point once the last reduction is done
     // (the reductions run in order on nu_stream)
-    CK(h, cudaStreamWaitEvent(h->stream, h->nu_red[(nsteps - 1) & 1], 0));
+    if (e == cudaSuccess && (e = cudaStreamWaitEvent(h->stream, h->nu_red[(nsteps - 1) & 1], 0)) != cudaSuccess)
+        where = "join of the reduction stream";
+    if (e != cudaSuccess) {
+        (void)cudaStreamSynchronize(h->nu_stream);  // no reduction keeps running beside later work
+        return cuda_fail(h, e, where);
+    }
     return LBM_OK;
 }
 
