@@ -86,9 +86,23 @@ def guo_source(rho0, ux, uy, Fx, Fy, phi):
     return _col(W, ux) * rho0 * (eF / CS2 + eu * eF / (phi * CS2 ** 2) - uF / (phi * CS2))
 
 
+def ergun_field(phi, phi_bar, K_bar, forchheimer=True):
+    """Per-cell K and F_phi of Eq. 5 for a porosity field, with the particle
+    diameter fixed by K(phi_bar) = K_bar."""
+    phi = np.asarray(phi, float)
+    if phi.ndim == 0 and phi == phi_bar:  # uniform porosity: K_bar itself (also at phi = 1)
+        K = np.float64(K_bar)
+    else:
+        K = K_bar * (phi / phi_bar) ** 3 * ((1 - phi_bar) / (1 - phi)) ** 2
+    Fphi = 1.75 / np.sqrt(150 * phi ** 3) if forchheimer else np.zeros_like(phi)
+    return K, Fphi
+
+
 class Restated:
-    """Side-heated cavity with walls on all four edges (thermal_bc 0,
-    adiabatic order 1), uniform porosity."""
+    """Cavity with walls on all four edges.  p["phi"], p["K"], p["Fphi"] are
+    scalars or (ny, nx) fields; p.get("thermal_bc"): 0 side-heated (T_h left,
+    T_c right, adiabatic top and bottom), 1 every wall at T_c;
+    p.get("adiabatic_order"): 1 (T_b = T_f) or 2 (T_b = (4 T_f - T_ff) / 3)."""
 
     def __init__(self, p: dict):
         self.p = p
@@ -126,10 +140,18 @@ class Restated:
         ux, uy, P, T, _, _ = self._macros(f, g)
         yy, xx = np.indices((ny, nx))
         yf, xf = yy + dy, xx + dx
-        Pb = P[yf, xf]  # uniform porosity: p_b = p_f  <=>  P_b = P_f
-        Tb = T[yf, xf].copy()
-        Tb[:, 0] = p["Th"]
-        Tb[:, -1] = p["Tc"]
+        phi = np.broadcast_to(np.asarray(p["phi"], float), (ny, nx))
+        Pb = phi * P[yf, xf] / phi[yf, xf]  # p_b = p_f with P = phi p
+        if p.get("adiabatic_order", 1) == 2:
+            yff, xff = np.clip(yy + 2 * dy, 0, ny - 1), np.clip(xx + 2 * dx, 0, nx - 1)
+            Tb = (4 * T[yf, xf] - T[yff, xff]) / 3
+        else:
+            Tb = T[yf, xf].copy()
+        if p.get("thermal_bc", 0) == 1:
+            Tb[:] = p["Tc"]
+        else:
+            Tb[:, 0] = p["Th"]
+            Tb[:, -1] = p["Tc"]
         return Pb, Tb
 
     def wall_rule(self, f, g):

@@ -420,6 +420,52 @@ def test_whole_step_matches_independent_restatement(shape):
     assert np.abs(ux).max() > 1e-5  # the check exercised a moving fluid
 
 
+@pytest.mark.parametrize("variant", ["adiabatic_order_2", "porosity_field", "cooled_walls_heat_source",
+                                     "side_heated_heat_source", "no_forchheimer"])
+def test_whole_step_variants_match_independent_restatement(variant):
+    # the wall and source variants the GPU path is compared with the oracle on:
+    # second-order adiabatic walls, a per-cell porosity field (Ergun per cell,
+    # p_b = p_f across the wall), every wall at T_c with a heat source
+    # (Section 4.2), side heating with a source (Section 4.3), Brinkman only
+    nx, ny = 8, 7
+    field = None
+    if variant == "cooled_walls_heat_source":
+        lat = derive(nx, ny, Ra=0.0, Da=1e-2, phi=1.0, Pr=7.0, RaI=6.4e5, thermal_bc=1)
+        lat.forchheimer = 0
+    elif variant == "side_heated_heat_source":
+        lat = derive(nx, ny, Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e7)
+    else:
+        lat = derive(nx, ny, Ra=1e4, Da=1e-2, phi=0.6)
+    if variant == "adiabatic_order_2":
+        lat.adiabatic_order = 2
+    if variant == "no_forchheimer":
+        lat.forchheimer = 0
+    if variant == "porosity_field":
+        field = np.random.default_rng(11).uniform(0.35, 0.85, (ny, nx))
+    lat.gbeta = 2e-3  # strong coupling so every term matters (also with Ra = 0)
+    o = Oracle(lat, phi_field=field)
+    f, g = o.state()
+    rng = np.random.default_rng(7)
+    f = f + rng.uniform(-2e-3, 2e-3, f.shape)
+    g = g + rng.uniform(-2e-2, 2e-2, g.shape)
+    o.set_state(f, g)
+    phi = lat.phi_bar if field is None else field
+    K, Fphi = R.ergun_field(phi, lat.phi_bar, lat.K_bar, bool(lat.forchheimer))
+    p = dict(rho0=lat.rho0, T0=lat.T0, gbeta=lat.gbeta, Gx=lat.Gx, Gy=lat.Gy, phi=phi, K=K, nu=lat.nu,
+             Fphi=Fphi, sigma=lat.sigma, varpi=lat.varpi, Q=lat.Q, s=list(lat.s), zeta=list(lat.zeta),
+             Th=lat.Th, Tc=lat.Tc, thermal_bc=lat.thermal_bc, adiabatic_order=lat.adiabatic_order)
+    rs = R.Restated(p)
+    Pb, Tb = rs.imposed(f, g)
+    for _ in range(10):
+        f, g, Pb, Tb = rs.step(f, g, Pb, Tb)
+        o.step(1)
+        fo, go = o.state()
+        np.testing.assert_allclose(fo, f, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(go, g, rtol=0, atol=1e-14)
+    ux, uy, pp, T = o.macros()
+    assert np.abs(ux).max() > 1e-6  # the check exercised a moving fluid
+
+
 # ---- the paper's printed results ---------------------------------------------
 
 def _golden(name):
