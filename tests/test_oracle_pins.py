@@ -421,12 +421,13 @@ def test_whole_step_matches_independent_restatement(shape):
 
 
 @pytest.mark.parametrize("variant", ["adiabatic_order_2", "porosity_field", "cooled_walls_heat_source",
-                                     "side_heated_heat_source", "no_forchheimer"])
+                                     "side_heated_heat_source", "no_forchheimer", "no_darcy"])
 def test_whole_step_variants_match_independent_restatement(variant):
     # the wall and source variants the GPU path is compared with the oracle on:
     # second-order adiabatic walls, a per-cell porosity field (Ergun per cell,
     # p_b = p_f across the wall), every wall at T_c with a heat source
-    # (Section 4.2), side heating with a source (Section 4.3), Brinkman only
+    # (Section 4.2), side heating with a source (Section 4.3), Brinkman only,
+    # and the pure-fluid limit Da = infinity (no drag at all; Tables 3-4)
     nx, ny = 8, 7
     field = None
     if variant == "cooled_walls_heat_source":
@@ -434,6 +435,9 @@ def test_whole_step_variants_match_independent_restatement(variant):
         lat.forchheimer = 0
     elif variant == "side_heated_heat_source":
         lat = derive(nx, ny, Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e7)
+    elif variant == "no_darcy":
+        lat = derive(nx, ny, Ra=1e5, Da=float("inf"), phi=1.0, Pr=0.71)
+        lat.forchheimer = 0
     else:
         lat = derive(nx, ny, Ra=1e4, Da=1e-2, phi=0.6)
     if variant == "adiabatic_order_2":
