@@ -466,7 +466,16 @@ def test_whole_step_variants_match_independent_restatement(variant):
         fo, go = o.state()
         np.testing.assert_allclose(fo, f, rtol=0, atol=1e-14)
         np.testing.assert_allclose(go, g, rtol=0, atol=1e-14)
+    # the macroscopic fields the parity tests compare: Eq. 21, 23, 36 off the
+    # walls, the imposed u = 0, p_b, T_b on them; p = P / phi
     ux, uy, pp, T = o.macros()
+    rux, ruy, rP, rT, _, _ = rs._macros(f, g)
+    wall, _, _ = rs._edges(ny, nx)
+    phin = np.broadcast_to(np.asarray(phi, float), (ny, nx))
+    np.testing.assert_allclose(ux, np.where(wall, 0.0, rux), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(uy, np.where(wall, 0.0, ruy), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(T, np.where(wall, Tb, rT), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(pp, np.where(wall, Pb, rP) / phin, rtol=0, atol=1e-14)
     assert np.abs(ux).max() > 1e-6  # the check exercised a moving fluid
 
 
