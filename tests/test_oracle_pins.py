@@ -479,6 +479,21 @@ def test_whole_step_variants_match_independent_restatement(variant):
     assert np.abs(ux).max() > 1e-6  # the check exercised a moving fluid
 
 
+def test_threaded_steps_do_not_depend_on_the_thread_count():
+    # the parity tests run the oracle on all host cores: its threaded passes
+    # must give the single-thread result bit for bit (no races, no
+    # order-dependent sums), here with a porosity field and a heat source
+    nx, ny = 23, 17
+    lat = derive(nx, ny, Ra=1e5, Da=1e-2, phi=0.4, Pr=0.7, RaI=1e6)
+    field = np.random.default_rng(3).uniform(0.3, 0.6, (ny, nx))
+    runs = []
+    for threads in (1, 3, 8):
+        o = Oracle(lat, phi_field=field).step(60, threads=threads)
+        runs.append(o.state())
+    for f, g in runs[1:]:
+        assert np.array_equal(f, runs[0][0]) and np.array_equal(g, runs[0][1])
+
+
 # ---- the paper's printed results ---------------------------------------------
 
 def _golden(name):
