@@ -305,7 +305,11 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic);
 /* Steps taken, number of tiles and blocks of the persistent launch. */
 int lbm_batch_query(lbm_batch b, long* t, int* ntiles, int* nblocks);
+/* Releases every resource of the batch (synchronises its stream first);
+ * NULL is a no-op. */
 int lbm_batch_destroy(lbm_batch b);
+/* Text of the last error of b, or of the last failed lbm_batch_init or
+ * lbm_init when b is NULL; valid until the next call on b. */
 const char* lbm_batch_last_error(lbm_batch b);
 
 /* Current time step count and divergence status (synchronises the stream). */
