@@ -129,3 +129,56 @@ def test_package_import_loads_nothing_and_fails_loudly_without_library(tmp_path)
     finally:
         _lib._lib = saved
 
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "lbm.h"
+
+typedef void (*entry_point)(void);
+/* every entry point the header declares: all must resolve at link time */
+static const entry_point declared[] = {
+%s
+};
+
+int main(void) {
+    lbm_params p;
+    lbm_handle h = NULL;
+    int rc;
+    lbm_params_default(&p, 64, 64, 1e4, 1e-2, 0.6);
+    p.phi = 1.5;
+    rc = lbm_init(&p, NULL, &h);
+    if (rc != LBM_ERR_ARG || h != NULL || !strstr(lbm_last_error(NULL), "phi")) return 1;
+    if (lbm_step(NULL, 1) != LBM_ERR_ARG || lbm_step_nusselt(NULL, 1, NULL) != LBM_ERR_ARG) return 2;
+    if (lbm_destroy(NULL) != LBM_OK || lbm_batch_destroy(NULL) != LBM_OK) return 3;
+    printf("%%d entry points\n", (int)(sizeof declared / sizeof declared[0]));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(lib, tmp_path):
+    # the boundary is a C ABI: a strict C99 program includes the header, links
+    # liblbm.so, takes the address of every declared entry point and gets the
+    # host-side argument errors (no device call)
+    import shutil
+    import subprocess
+
+    from paper_1308_2071_gb300.build import build
+
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM % ",\n".join(f"    (entry_point){n}" for n in names))
+    libdir = os.path.dirname(build())
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-llbm", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == f"{len(names)} entry points"
+
