@@ -479,6 +479,32 @@ def test_whole_step_variants_match_independent_restatement(variant):
     assert np.abs(ux).max() > 1e-6  # the check exercised a moving fluid
 
 
+@pytest.mark.parametrize("adiabatic_order", [1, 2])
+def test_side_heated_cavity_keeps_its_centro_symmetry(adiabatic_order):
+    # Rotating the side-heated cavity by 180 degrees swaps the hot and cold
+    # walls; with T -> -T the Boussinesq force phi G of Eq. 4 turns with the
+    # cavity, so the rest start evolves into a state with T = -T(rotated) and
+    # u = -u(rotated) at every step, and equal Nusselt numbers (Eq. 38) on
+    # both walls.  The walls are at +-1/2 (T0 = 0): the D2Q5 flux equilibrium
+    # u T / sigma (Eq. 29) takes the absolute temperature, so for T0 != 0 the
+    # map leaves a residual 2 T0 u and the discrete symmetry is only
+    # approximate (5e-4 in T after 100 steps at T0 = 1/2).  A wrong neighbour
+    # offset, direction or wall normal on one side breaks the symmetry.
+    lat = derive(21, 17, Ra=1e5, Da=1e-2, phi=0.6, Th=0.5, Tc=-0.5)
+    lat.adiabatic_order = adiabatic_order
+    o = Oracle(lat)
+    for _ in range(4):
+        o.step(100, threads=4)
+        ux, uy, p, T = o.macros()
+        rot = lambda a: a[::-1, ::-1]
+        assert np.abs(ux).max() > 1e-4  # a developed flow, not the rest state
+        np.testing.assert_allclose(T - lat.T0, -(rot(T) - lat.T0), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(ux, -rot(ux), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(uy, -rot(uy), rtol=0, atol=1e-13)
+        nl, nr = o.nusselt()
+        assert abs(nl - nr) < 1e-12 * abs(nl), (nl, nr)
+
+
 def test_threaded_steps_do_not_depend_on_the_thread_count():
     # the parity tests run the oracle on all host cores: its threaded passes
     # must give the single-thread result bit for bit (no races, no
