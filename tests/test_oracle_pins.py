@@ -505,6 +505,20 @@ def test_side_heated_cavity_keeps_its_centro_symmetry(adiabatic_order):
         assert abs(nl - nr) < 1e-12 * abs(nl), (nl, nr)
 
 
+def test_hot_fluid_rises_at_the_hot_wall():
+    # buoyancy G = g beta (T - T0) j (Eq. 4, Section 2) with j pointing up:
+    # in x-right, y-up axes the cell turns clockwise, up the hot wall (x = 0),
+    # towards the cold wall along the top, down the cold wall and back along
+    # the bottom.  Nusselt numbers are blind to a flipped gravity (the
+    # mirrored flow has the same Nu), so the direction is checked here.
+    lat = derive(21, 17, Ra=1e5, Da=1e-2, phi=0.6)
+    o = Oracle(lat).step(300, threads=4)
+    ux, uy, p, T = o.macros()
+    mid = 17 // 2
+    assert uy[mid, 1:4].min() > 0 and uy[mid, -4:-1].max() < 0
+    assert ux[-3, 8:13].min() > 0 and ux[2, 8:13].max() < 0
+
+
 def test_threaded_steps_do_not_depend_on_the_thread_count():
     # the parity tests run the oracle on all host cores: its threaded passes
     # must give the single-thread result bit for bit (no races, no
