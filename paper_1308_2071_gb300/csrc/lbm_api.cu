@@ -461,6 +461,7 @@ int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype) {
 }
 
 int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, int* nodes_per_thread) {
+    TraceRange trace_("lbm_tune");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     char sig[256];
     {
@@ -545,6 +546,7 @@ int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, i
 }
 
 int lbm_step(lbm_handle h, long nsteps) {
+    TraceRange trace_("lbm_step");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     long left = nsteps;
@@ -567,6 +569,7 @@ int lbm_step(lbm_handle h, long nsteps) {
 }
 
 int lbm_observables(lbm_handle h, lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev, void* p_dev) {
+    TraceRange trace_("lbm_observables");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     ObserveLaunch L;
     L.precision = h->precision;
@@ -645,6 +648,7 @@ int enqueue_nusselt(lbm_handle h, double* out) {
 }  // namespace
 
 int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
+    TraceRange trace_("lbm_nusselt");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     int rc = enqueue_nusselt(h, h->nu_dev);
     if (rc != LBM_OK) return rc;
@@ -656,6 +660,7 @@ int lbm_nusselt(lbm_handle h, double* nu_hot, double* nu_cold) {
 }
 
 int lbm_nusselt_async(lbm_handle h, double* out2) {
+    TraceRange trace_("lbm_nusselt_async");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!out2) return fail(h, LBM_ERR_ARG, "out2 is NULL");
     // device memory and mapped (pinned) host memory: the kernel writes there
@@ -668,6 +673,7 @@ int lbm_nusselt_async(lbm_handle h, double* out2) {
 }
 
 int lbm_step_nusselt(lbm_handle h, long nsteps, double* out) {
+    TraceRange trace_("lbm_step_nusselt");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return LBM_OK;
@@ -742,6 +748,7 @@ int lbm_step_nusselt(lbm_handle h, long nsteps, double* out) {
 }
 
 int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void* dJdphi_dev) {
+    TraceRange trace_("lbm_adjoint_step");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "the adjoint needs a handle created with use_phi_field = 1");
     if (h->precision != LBM_F64 && h->precision != LBM_F32)
@@ -820,6 +827,7 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
 }
 
 int lbm_run_steady(lbm_handle h, double tol, long check_every, long max_steps, long* steps_taken, double* change) {
+    TraceRange trace_("lbm_run_steady");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!(tol > 0.0) || check_every < 1 || max_steps < 1) return fail(h, LBM_ERR_ARG, "need tol > 0, check_every >= 1, max_steps >= 1");
     const long K = (check_every + 1) / 2 * 2;  // even: the captured buffers return to their parity
@@ -892,6 +900,7 @@ int lbm_checkpoint_size(lbm_handle h, size_t* bytes) {
 }
 
 int lbm_save(lbm_handle h, void* host, size_t bytes) {
+    TraceRange trace_("lbm_save");
     if (!h || !host) return fail(h, LBM_ERR_ARG, "handle and host buffer are required");
     size_t need = sizeof(CkptHeader) + h->buf_bytes;
     if (bytes < need) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
@@ -913,6 +922,7 @@ int lbm_save(lbm_handle h, void* host, size_t bytes) {
 }
 
 int lbm_load(lbm_handle h, const void* host, size_t bytes) {
+    TraceRange trace_("lbm_load");
     if (!h || !host) return fail(h, LBM_ERR_ARG, "handle and host buffer are required");
     CkptHeader hd;
     if (bytes < sizeof hd) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");

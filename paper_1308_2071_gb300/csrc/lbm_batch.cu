@@ -693,6 +693,7 @@ int lbm_batch_init(const lbm_params* p, int ncav, void* stream, lbm_batch* out) 
 }
 
 int lbm_batch_step(lbm_batch b, long nsteps) {
+    TraceRange trace_("lbm_batch_step");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps < 0");
     // one launch runs at most 2^16 steps: the dataflow mode's per-cavity
@@ -709,6 +710,7 @@ int lbm_batch_step(lbm_batch b, long nsteps) {
 }
 
 int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold) {
+    TraceRange trace_("lbm_batch_nusselt");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     const int prev = b->par ^ 1;
     if (b->precision == LBM_F64)
@@ -774,6 +776,7 @@ int lbm_batch_set_wait_limit(lbm_batch b, long long polls) {
 }
 
 int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h, int* blocks_per_sm) {
+    TraceRange trace_("lbm_batch_tune");
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     TuneChoice best;
     bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);

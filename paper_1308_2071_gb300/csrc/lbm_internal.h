@@ -7,10 +7,22 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Names one call of the C-ABI in a profiler's timeline (an NVTX range for the
+// call's duration on the host); costs next to nothing when no profiler is
+// attached.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Lattice parameters derived from lbm_params (Section 4 set-up).
 struct Derived {
