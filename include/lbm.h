@@ -37,14 +37,20 @@ extern "C" {
 #define LBM_ERR_TIMEOUT 4  /* a bounded device-side wait ran out                          */
 #define LBM_ERR_STATE 5    /* call out of order (e.g. adjoint before any forward state)   */
 
-/* storage / arithmetic precision of the populations */
+/* Storage / arithmetic precision of the populations.  Populations are stored
+ * as deviations from the rest state.  The FP32-arithmetic variants keep the
+ * thermal populations relative to a per-node temperature frame (one more
+ * plane: the node's T - T0 when it was last written), so that the stored
+ * values stay small and FP32 keeps the slow late-time evolution of T (plain
+ * FP32 deviations g_j - w~_j T0 of up to 0.3 lose changes below 3e-8 per
+ * step).  Bytes moved per node and step: 224, 114, 78, 120. */
 #define LBM_F64 0            /* FP64 storage, FP64 arithmetic                       */
-#define LBM_F32 1            /* FP32 storage of deviations, FP32 arithmetic         */
-#define LBM_F32_STORE_F16 2  /* FP16 storage of deviations, FP32 arithmetic         */
-#define LBM_F32_FRAMED 3     /* FP32 storage, thermal populations relative to a per-
-                                node temperature frame (one more plane), FP32
-                                arithmetic: resolves slow late-time evolution that
-                                plain FP32 storage of g_j - w~_j T0 loses           */
+#define LBM_F32 1            /* FP32 storage, 8-bit temperature frame (a power-of-
+                                two quantum fq: F = k fq), FP32 arithmetic          */
+#define LBM_F32_STORE_F16 2  /* FP16 flow storage, FP32 thermal storage with the
+                                8-bit temperature frame, FP32 arithmetic            */
+#define LBM_F32_FRAMED 3     /* FP32 storage, FP32 temperature frame, FP32
+                                arithmetic                                          */
 
 /* thermal boundary layouts */
 #define LBM_BC_SIDE_HEATED 0 /* Section 4.1: left T_h, right T_c, top/bottom adiabatic */
@@ -74,7 +80,8 @@ typedef struct {
     int adiabatic_order; /* 1: T_b = T_f on adiabatic walls; 2: T_b = (4T_f - T_ff)/3   */
     int collision;       /* LBM_MRT or LBM_LBGK                                          */
     int block_x, block_y;/* launch shape of the step kernel; 0 = library default        */
-    int nodes_per_thread;/* 1 or 2 nodes per thread along y; 0 = library default        */
+    int nodes_per_thread;/* 1: one node per thread; 2: two along y; 3: two side by side
+                            along x (paired loads and stores); 0 = library default */
     double RaI;          /* internal Rayleigh number (Section 2); 0 = none.  With
                             LBM_BC_SIDE_HEATED: Q''' = (RaI/Ra) alpha_e (Th-Tc)/L^2
                             (Section 4.3); with LBM_BC_COOLED: tau_nu from RaI,
@@ -118,12 +125,20 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out);
  * values in (0, 1), dtype LBM_F64 (double) or LBM_F32 (float); the caller
  * keeps ownership, the library copies it (to float for the FP32 and
  * FP16-storage paths, double for FP64).  Requires
- * use_phi_field = 1.  Resets the state to the initial state (t = 0).
+ * use_phi_field = 1.  Resets the state to the initial state (t = 0).  The
+ * values are checked on the device first (the call synchronises the stream):
+ * a field with any value outside (0, 1), NaN included, is rejected with
+ * LBM_ERR_ARG and leaves the handle as it was.
  * Errors: LBM_ERR_ARG, LBM_ERR_STATE (use_phi_field = 0), LBM_ERR_CUDA. */
 int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype);
 
+/* Restarts the cavity from the initial state of lbm_init (t = 0), keeping its
+ * parameters, porosity field and launch shape; stream-ordered.  Clears the
+ * divergence flag.  Errors: LBM_ERR_ARG (NULL), LBM_ERR_CUDA. */
+int lbm_reset(lbm_handle h);
+
 /* Autotuner of the step kernel: times candidate launch shapes (block_x x
- * block_y threads, 1 or 2 nodes per thread) on this lattice, keeps the
+ * block_y threads, nodes_per_thread 1, 2 or 3) on this lattice, keeps the
  * fastest and records it in a text cache at cache_path (NULL: no cache; one
  * line per device, precision, lattice size and porosity mode); a cached entry
  * is reused without timing.  Timing advances the lattice, so the handle is
@@ -208,7 +223,7 @@ int lbm_field_extrema(lbm_handle h, double* T_max, double* psi_min, double* psi_
  * compare the lattice with a reference implementation.  Stream-ordered. */
 int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev);
 
-/* Checkpoint / resume.  A checkpoint is a header (magic, version 2, nx, ny,
+/* Checkpoint / resume.  A checkpoint is a header (magic, version 3, nx, ny,
  * precision, t) and one state buffer, the post-collision lattice B_{n-1}
  * that the current post-stream state S_n is pulled from (Eq. 18, 35): every
  * observable at t_n comes from it, and lbm_load() rebuilds B_n from it with

@@ -59,6 +59,22 @@ __device__ __forceinline__ void gather_adjoint(const R* __restrict__ M, const Ge
     }
 }
 
+// The populations pulled into node off, as deviations from the rest state:
+// with framed storage the thermal values are re-expressed relative to T0
+// (the frame is an exact change of variables of the stored values, so the
+// adjoint of the step is the one of the plain deviations).
+template <class T>
+__device__ __forceinline__ void pull_rest(const Coef<typename T::R>& c, const Src<T>& src, const Geom& gm, int off,
+                                          typename T::R (&d)[9], typename T::R (&h)[5]) {
+    pull<T>(src, gm, off, d, h);
+    if constexpr (Framed<T>::value) {
+        const typename T::R F = frame_in<T>(c, src, gm, off, h);
+        h[0] += c.wt0 * F;
+#pragma unroll
+        for (int j = 1; j < 5; ++j) h[j] += c.wt1 * F;
+    }
+}
+
 __device__ __forceinline__ bool wall_is_dirichlet(const Geom& gm, Normal nr) {
     return gm.thermal_bc == 1 || nr.dx != 0;
 }
@@ -90,7 +106,7 @@ __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename
         gather_adjoint<R>(Mnext, gm, x, y, lf, lh);
         const int xf = x + nr.dx, yf = y + nr.dy, offf = yf * gm.pitch + xf;
         R df[9], hf[5];
-        pull<T>(state, gm, offf, df, hf);
+        pull_rest<T>(c, state, gm, offf, df, hf);
         Tape<R> tf;
         tape_node<R>(c, (R)phi[offf], df, hf, tf);
         R dfb[9] = {R(0)}, hfb[5] = {R(0)}, pfb = R(0);
@@ -101,7 +117,7 @@ __device__ __forceinline__ void adjoint_node(const Src<T>& state, const typename
     }
     gather_adjoint<R>(Mnext, gm, x, y, lf, lh);
     R d[9], h[5];
-    pull<T>(state, gm, off, d, h);
+    pull_rest<T>(c, state, gm, off, d, h);
     Tape<R> t;
     tape_node<R>(c, (R)phi[off], d, h, t);
     R db[9] = {R(0)}, hb[5] = {R(0)}, pb = R(0);
@@ -284,6 +300,7 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
 namespace lbm {
 cudaError_t launch_adjoint_sweep(const AdjointJob& J) {
     if (J.precision == PREC_F64) return adjoint_sweep<PrecF64>(J);
-    return adjoint_sweep<PrecF32>(J);
+    if (J.precision == PREC_F32T) return adjoint_sweep<PrecF32T>(J);
+    return adjoint_sweep<PrecF32Q>(J);
 }
 }  // namespace lbm

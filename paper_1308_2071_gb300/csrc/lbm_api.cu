@@ -166,6 +166,16 @@ void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
         c->a_lin = (R)0;
         c->a_quad = (R)0;
     }
+    // 8-bit temperature frames: the power of two fq whose 128 steps span the
+    // largest |T - T0| expected, the wall temperatures plus the conduction
+    // maximum Q L^2 / (8 alpha_e) of a heat source (alpha_e from A9); a
+    // larger |T - T0| only saturates the frame, which costs precision, not
+    // correctness
+    const double alpha = p->sigma * (4.0 + p->varpi) / 10.0 * (dv.tau_T - 0.5);
+    const double tspan = fmax(fabs(p->Th - dv.T0), fabs(p->Tc - dv.T0)) + fabs(dv.Q) * dv.L * dv.L / (8.0 * alpha);
+    const double fq = exp2(ceil(log2(tspan / 128.0)));
+    c->fq = (R)fq;
+    c->ifq = (R)(1.0 / fq);
 }
 
 }  // namespace
@@ -379,13 +389,15 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out) {
     h->p = *p;
     h->precision = p->precision;
     const long plane = h->gm.plane;
-    h->bx = p->block_x > 0 ? p->block_x : (p->nx <= 64 ? 64 : 128);
-    h->by = p->block_y > 0 ? p->block_y : 256 / h->bx;
-    // FP16-flow lattices move 38 B per node each way: two nodes per thread by default
-    h->npt = p->nodes_per_thread > 0 ? p->nodes_per_thread : (p->precision == LBM_F32_STORE_F16 ? 2 : 1);
-    if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0 || h->npt > 2) {
+    // defaults (the autotuner's picks on the 4096^2 benchmark lattice): FP32
+    // arithmetic two nodes side by side along x in 128-thread blocks, FP64 two
+    // nodes along y
+    h->bx = p->block_x > 0 ? p->block_x : (p->nx <= 128 ? 32 : 64);
+    h->by = p->block_y > 0 ? p->block_y : (h->bx >= 128 ? 1 : 128 / h->bx);
+    h->npt = p->nodes_per_thread > 0 ? p->nodes_per_thread : (p->precision == LBM_F64 ? 2 : 3);
+    if (h->bx * h->by > 256 || h->bx <= 0 || h->by <= 0 || h->npt > 3) {
         delete h;
-        return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256 and nodes_per_thread 1 or 2");
+        return fail(nullptr, LBM_ERR_ARG, "block_x * block_y must be <= 256 and nodes_per_thread 1, 2 or 3");
     }
     h->stream = (cudaStream_t)stream;
     h->buf_bytes = state_buffer_bytes(p->precision, (int)plane);
@@ -455,8 +467,24 @@ int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype) {
     if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "handle was created with use_phi_field = 0");
     if (!phi_dev) return fail(h, LBM_ERR_ARG, "phi_dev is NULL");
     if (dtype != LBM_F64 && dtype != LBM_F32) return fail(h, LBM_ERR_ARG, "dtype must be LBM_F64 or LBM_F32");
+    // every cell must lie in (0, 1): a 0 would make 1/phi infinite, a 1 or more
+    // the Ergun drag zero or negative (Eq. 5); the count lands in the
+    // partial-sum scratch, which no other call uses concurrently
+    unsigned long long* bad = (unsigned long long*)h->partials;
+    unsigned long long nbad = 0;
+    CK(h, cudaMemsetAsync(bad, 0, sizeof *bad, h->stream));
+    CK(h, launch_count_bad_phi(phi_dev, dtype == LBM_F64, (long)h->p.nx * h->p.ny, bad, kReduceBlocks, h->stream));
+    CK(h, cudaMemcpyAsync(h->obs_host, bad, sizeof nbad, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    memcpy(&nbad, h->obs_host, sizeof nbad);
+    if (nbad) return fail(h, LBM_ERR_ARG, std::to_string(nbad) + " porosity values outside (0, 1)");
     CK(h, launch_convert_phi(phi_dev, dtype == LBM_F64, h->phi, h->precision, h->gm, kReduceBlocks, h->stream));
     drop_graphs(h);
+    return reset_state(h);
+}
+
+int lbm_reset(lbm_handle h) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     return reset_state(h);
 }
 
@@ -492,8 +520,9 @@ int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, i
         }
     }
     if (!cached) {
-        const int cand[][3] = {{128, 2, 1}, {64, 4, 1},  {256, 1, 1}, {32, 8, 1}, {128, 1, 2},
-                               {64, 2, 2},  {128, 2, 2}, {256, 1, 2}, {32, 4, 2}};
+        const int cand[][3] = {{128, 2, 1}, {64, 4, 1}, {256, 1, 1}, {32, 8, 1}, {128, 1, 2}, {64, 2, 2},
+                               {128, 2, 2}, {256, 1, 2}, {32, 4, 2}, {32, 8, 3}, {64, 4, 3}, {128, 2, 3},
+                               {64, 2, 3},  {128, 1, 3}, {256, 1, 3}};
         cudaEvent_t e0, e1;
         CK(h, cudaEventCreate(&e0));
         CK(h, cudaEventCreate(&e1));
@@ -751,8 +780,8 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
     TraceRange trace_("lbm_adjoint_step");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!h->p.use_phi_field) return fail(h, LBM_ERR_STATE, "the adjoint needs a handle created with use_phi_field = 1");
-    if (h->precision != LBM_F64 && h->precision != LBM_F32)
-        return fail(h, LBM_ERR_ARG, "the adjoint runs in LBM_F64 or LBM_F32");
+    if (h->precision != LBM_F64 && h->precision != LBM_F32 && h->precision != LBM_F32_FRAMED)
+        return fail(h, LBM_ERR_ARG, "the adjoint runs in LBM_F64, LBM_F32 or LBM_F32_FRAMED");
     if (h->p.adiabatic_order != 1) return fail(h, LBM_ERR_ARG, "the adjoint supports first-order adiabatic walls");
     if (nsteps < 1 || ckpt_every < 1 || !dJdphi_dev) return fail(h, LBM_ERR_ARG, "need nsteps >= 1, ckpt_every >= 1, output");
     const long N = nsteps, K = ckpt_every < nsteps ? ckpt_every : nsteps;
@@ -907,7 +936,7 @@ int lbm_save(lbm_handle h, void* host, size_t bytes) {
     CkptHeader hd;
     memset(&hd, 0, sizeof hd);
     memcpy(hd.magic, "LBMCKPT", 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.nx = h->p.nx;
     hd.ny = h->p.ny;
     hd.precision = h->precision;
@@ -927,8 +956,10 @@ int lbm_load(lbm_handle h, const void* host, size_t bytes) {
     CkptHeader hd;
     if (bytes < sizeof hd) return fail(h, LBM_ERR_ARG, "checkpoint buffer too small");
     memcpy(&hd, host, sizeof hd);
-    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || (hd.version != 1 && hd.version != 2))
+    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || hd.version < 1 || hd.version > 3)
         return fail(h, LBM_ERR_ARG, "not a checkpoint");
+    if (!ckpt_layout_current(hd.version, hd.precision))
+        return fail(h, LBM_ERR_ARG, "checkpoint written with an older storage layout of this precision");
     const long nbuf = hd.version == 1 ? 2 : 1;
     if (hd.nx != h->p.nx || hd.ny != h->p.ny || hd.precision != h->precision ||
         hd.payload != (long)(nbuf * h->buf_bytes) || bytes < sizeof hd + nbuf * h->buf_bytes)

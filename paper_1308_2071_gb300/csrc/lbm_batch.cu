@@ -413,7 +413,7 @@ const void* batch_kernel(int precision, int npt, bool split) {
     if (precision == LBM_F64) return kernel_ptr<PrecF64P, false>(npt);
     if (precision == LBM_F32_FRAMED)
         return split ? kernel_ptr<PrecF32TP, true>(npt) : kernel_ptr<PrecF32TP, false>(npt);
-    return split ? kernel_ptr<PrecF32P, true>(npt) : kernel_ptr<PrecF32P, false>(npt);
+    return split ? kernel_ptr<PrecF32QP, true>(npt) : kernel_ptr<PrecF32QP, false>(npt);
 }
 
 int npt_of(const TuneChoice& t) { return tile_nodes(t) == 2 * block_of(t) ? 2 : 1; }
@@ -720,7 +720,7 @@ int lbm_batch_nusselt(lbm_batch b, double* nu_hot, double* nu_cold) {
         k_batch_nusselt<PrecF32TP><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
                                                                   b->nu_dev);
     else
-        k_batch_nusselt<PrecF32P><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
+        k_batch_nusselt<PrecF32QP><<<b->ncav, 256, 0, b->stream>>>((const CavDesc<float>*)b->descs, prev, b->Ls,
                                                                  b->nu_dev);
     BCK(b, cudaGetLastError());
     std::vector<double> h(2 * b->ncav);

@@ -42,6 +42,13 @@ struct CkptHeader {
     long payload;
 };
 
+// Version 3 stores LBM_F32 and LBM_F32_STORE_F16 lattices with their 8-bit
+// temperature frames; the FP64 and FP32-framed layouts are those of versions
+// 1 and 2, which stay readable.
+inline bool ckpt_layout_current(int version, int precision) {
+    return version == 3 || precision == LBM_F64 || precision == LBM_F32_FRAMED;
+}
+
 // Error text returned by lbm_last_error(NULL) (calls without a handle).
 void set_global_error(const std::string& msg);
 
@@ -62,7 +69,7 @@ struct StepLaunch {
     const void* phi;  // per-cell porosity in the storage type, or nullptr
     Geom gm;
     int bx, by;
-    int npt = 1;  // nodes per thread along y (1 or 2)
+    int npt = 1;  // nodes per thread: 1, 2 (along y) or 3 (two along x)
     int* status;
     cudaStream_t stream;
     bool pdl = false;  // launch as a programmatic dependent of the previous step
@@ -145,6 +152,9 @@ cudaError_t launch_extrema(int precision, const void* prev, const void* phi, con
 size_t state_buffer_bytes(int precision, int plane);
 size_t phi_bytes(int precision, int plane);
 
+// Adds the number of the n values of in outside (0, 1), NaN included, to *bad.
+cudaError_t launch_count_bad_phi(const void* in, int in_is_double, long n, unsigned long long* bad, int nblocks,
+                                 cudaStream_t s);
 cudaError_t launch_convert_phi(const void* in, int in_is_double, void* out, int precision, const Geom& gm,
                                int nblocks, cudaStream_t s);
 

@@ -4,8 +4,10 @@
 // sums of every block, the result and a status word) lives in one file-scope
 // static device array that every device loading the library keeps until the
 // process exits.
-#include <mutex>
+#include <math.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "lbm_internal.h"
 
@@ -75,9 +77,10 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
     cudaError_t e = cudaMemcpyAsync(&hd, ckpt_dev, sizeof hd, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("header read: ") + cudaGetErrorString(e));
-    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || (hd.version != 1 && hd.version != 2))
-        return fail(LBM_ERR_ARG, "not a checkpoint");
-    // both versions start with B_{n-1}, the only buffer read here
+    if (memcmp(hd.magic, "LBMCKPT", 8) != 0 || hd.version < 1 || hd.version > 3 ||
+        !ckpt_layout_current(hd.version, hd.precision))
+        return fail(LBM_ERR_ARG, "not a checkpoint of the current storage layout");
+    // every version starts with B_{n-1}, the only buffer read here
     const long nbuf = hd.version == 1 ? 2 : 1;
     if (hd.nx != p->nx || hd.ny != p->ny || hd.precision != p->precision || hd.payload != (long)(nbuf * buf) ||
         bytes < sizeof(CkptHeader) + nbuf * buf)
@@ -122,7 +125,12 @@ int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t by
     out->residual = 0.0;
     out->mass = n + o[4];
     out->heat = n * dv.T0 + o[5];
-    out->status = LBM_OK;
+    // the state's own divergence test (the step kernels' flag is not part of a
+    // checkpoint): a non-finite value or |u| >= 1/2 anywhere; a NaN anywhere
+    // makes the maximum NaN
+    const bool diverged = !(o[2] < 0.5) || !isfinite(o[4]) || !isfinite(o[5]);
+    out->status = diverged ? LBM_ERR_DIVERGED : LBM_OK;
+    if (diverged) return fail(LBM_ERR_DIVERGED, "the checkpoint holds a non-finite value or |u| >= 1/2");
     return LBM_OK;
 }
 

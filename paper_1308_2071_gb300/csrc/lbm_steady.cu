@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_extrema(Src<T> prev, const typename T::
 
 template <class T> static const Coef<typename T::R>& coef_sel(const CoefSet& cs);
 template <> const Coef<double>& coef_sel<PrecF64>(const CoefSet& cs) { return cs.d; }
-template <> const Coef<float>& coef_sel<PrecF32>(const CoefSet& cs) { return cs.f; }
+template <> const Coef<float>& coef_sel<PrecF32Q>(const CoefSet& cs) { return cs.f; }
 template <> const Coef<float>& coef_sel<PrecF16>(const CoefSet& cs) { return cs.f; }
 template <> const Coef<float>& coef_sel<PrecF32T>(const CoefSet& cs) { return cs.f; }
 
@@ -85,7 +85,7 @@ static cudaError_t launch_check_t(const SteadyCheckLaunch& L, const CoefSet& cs)
 cudaError_t launch_steady_check(const SteadyCheckLaunch& L, const CoefSet& cs) {
     switch (L.precision) {
         case PREC_F64: return launch_check_t<PrecF64>(L, cs);
-        case PREC_F32: return launch_check_t<PrecF32>(L, cs);
+        case PREC_F32: return launch_check_t<PrecF32Q>(L, cs);
         case PREC_F32T: return launch_check_t<PrecF32T>(L, cs);
         default: return launch_check_t<PrecF16>(L, cs);
     }
@@ -103,7 +103,7 @@ cudaError_t launch_extrema(int precision, const void* prev, const void* phi, con
                            double* out, cudaStream_t s) {
     switch (precision) {
         case PREC_F64: return launch_extrema_t<PrecF64>(prev, phi, gm, cs, out, s);
-        case PREC_F32: return launch_extrema_t<PrecF32>(prev, phi, gm, cs, out, s);
+        case PREC_F32: return launch_extrema_t<PrecF32Q>(prev, phi, gm, cs, out, s);
         case PREC_F32T: return launch_extrema_t<PrecF32T>(prev, phi, gm, cs, out, s);
         default: return launch_extrema_t<PrecF16>(prev, phi, gm, cs, out, s);
     }

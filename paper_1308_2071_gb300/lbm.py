@@ -97,6 +97,11 @@ class Cavity:
         L.check(L.load().lbm_tune(self._h, path, C.byref(bx), C.byref(by), C.byref(npt)), self._h)
         return bx.value, by.value, npt.value
 
+    def reset(self) -> "Cavity":
+        """Back to the initial state (t = 0), same parameters, field and launch shape."""
+        L.check(L.load().lbm_reset(self._h), self._h)
+        return self
+
     def step(self, n: int = 1) -> "Cavity":
         L.check(L.load().lbm_step(self._h, int(n)), self._h)
         return self

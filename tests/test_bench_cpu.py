@@ -61,3 +61,11 @@ def test_reference_arm_prints_one_line_with_the_oracle():
     assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+    # the same config keys as the GPU arm's line (workload, single GPU, one replica) and the requested warm-up
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert d["config"] == dict(bench.workload(64), parallelism="single GPU", replicas=1)
+    assert d["warmup"] == 1

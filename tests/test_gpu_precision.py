@@ -1,0 +1,72 @@
+"""Storage precision over the stated run length: every FP32-arithmetic storage
+variant of the library against the FP64 path after 50,000 steps of the
+throughput benchmark's physics (side-heated porous cavity, Ra = 1e6,
+Da = 1e-4, porosity 0.4, Ma = 0.1), at 1024^2.
+
+The FP64 path itself matches the FP64 oracle to 1e-10 over 2000 steps at
+this size (test_gpu_parity.py::test_config2_1024_long_run_matches_oracle), so
+it stands in for the oracle over the 50,000 steps the oracle would need
+hours for.
+
+Per-field bounds (max over the lattice): velocity max|du| / max|u|,
+temperature max|dT| / (T_h - T_c), both wall Nusselt numbers relative.
+FP32 storage: 1e-4, 1e-5, 1e-4.
+
+Why frames: late in the run T changes by about alpha dT / L^2 = 1e-8 per
+step, below the 3e-8 spacing of FP32 numbers near the 0.3 that a plain
+deviation g_0 - w~_0 T0 reaches at the hot wall; plain deviations lost that
+evolution (max|du|/max|u| 2.7e-4, max|dT| 1.05e-4, Nu 8.6e-4 at this size).
+Relative to a per-node temperature frame the stored values stay small.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N, STEPS = 1024, 50_000
+PHYS = dict(Ra=1e6, Da=1e-4, phi=0.4)
+BOUNDS = {  # velocity, temperature, Nusselt
+    "f32": (1e-4, 1e-5, 1e-4),
+    "f32t": (1e-4, 1e-5, 1e-4),
+}
+
+
+@pytest.fixture(scope="module")
+def runs():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_2071_gb300 import Cavity
+
+    res = {}
+
+    def work(prec):
+        c = Cavity(N, N, precision=prec, stream=torch.cuda.Stream(), **PHYS)
+        c.step(STEPS)
+        o = c.observables(fields=True)
+        res[prec] = dict(nu=(o["nu_hot"], o["nu_cold"]), status=o["status"],
+                         **{k: o[k].double().cpu().numpy() for k in ("ux", "uy", "T")})
+        c.close()
+
+    # the FP64 run takes about 25 s; the others run beside it on their own streams
+    th = [threading.Thread(target=work, args=(p,)) for p in ["f64", *BOUNDS]]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return res
+
+
+@pytest.mark.parametrize("precision", list(BOUNDS))
+def test_storage_variant_within_its_bounds_after_50k_steps(runs, precision):
+    ref, r = runs["f64"], runs[precision]
+    umax = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    eu = max(np.abs(r["ux"] - ref["ux"]).max(), np.abs(r["uy"] - ref["uy"]).max()) / umax
+    eT = np.abs(r["T"] - ref["T"]).max()
+    en = max(abs(r["nu"][k] - ref["nu"][k]) / abs(ref["nu"][k]) for k in (0, 1))
+    bu, bT, bn = BOUNDS[precision]
+    assert r["status"] == 0
+    assert eu < bu and eT < bT and en < bn, (precision, eu, eT, en)

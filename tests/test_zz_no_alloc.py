@@ -27,7 +27,7 @@ def _call(lib, _lib, params, dev, nbytes, fields, stream):
     return out
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "f32t"])
 def test_noalloc_matches_observables_on_consecutive_calls(precision):
     import torch
 
@@ -77,4 +77,38 @@ def test_noalloc_rejects_a_mismatched_checkpoint():
                                      None, None, None, None)
     assert rc == _lib.LBM_ERR_ARG
     assert "smaller" in lib.lbm_last_error(None).decode()
+    cav.close()
+
+
+def test_noalloc_reports_a_nonfinite_checkpoint_as_diverged():
+    # A checkpoint carries no divergence flag of the steps that made it, so the
+    # call tests the state itself: a NaN planted (on the host) into one
+    # population of the saved lattice makes max|u| NaN, which it reports as
+    # LBM_ERR_DIVERGED with status set, not as a finite maximum.
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1308_2071_gb300 import Cavity, _lib
+
+    lib = _lib.load()
+    nx, ny = 40, 32
+    cav = Cavity(nx, ny, Ra=1e5, Da=1e-2, phi=0.6, precision="f64")
+    cav.step(50)
+    blob = bytearray(cav.save())
+    # B_{n-1} follows the 40-byte header: FP64 planes with a row pitch of 48 values
+    arr = np.frombuffer(blob, dtype=np.float64, count=9 * 48 * ny, offset=40)
+    arr.setflags(write=True)
+    arr[1 * 48 * ny + 16 * 48 + 20] = np.nan  # plane 1 (east), node (20, 16)
+    dev = torch.frombuffer(blob, dtype=torch.uint8).to("cuda")
+    out = _lib.Obs()
+    rc = lib.lbm_observables_noalloc(C.byref(cav.params), C.c_void_p(dev.data_ptr()), len(blob),
+                                     C.c_void_p(cav.stream.cuda_stream), C.byref(out), None, None, None, None)
+    assert rc == _lib.LBM_ERR_DIVERGED and out.status == _lib.LBM_ERR_DIVERGED
+    assert out.umax != out.umax  # NaN
+    # the same call on the intact state is clean again (the status word is cleared on entry)
+    good = torch.frombuffer(bytearray(cav.save()), dtype=torch.uint8).to("cuda")
+    rc = lib.lbm_observables_noalloc(C.byref(cav.params), C.c_void_p(good.data_ptr()), good.numel(),
+                                     C.c_void_p(cav.stream.cuda_stream), C.byref(out), None, None, None, None)
+    assert rc == _lib.LBM_OK and out.status == _lib.LBM_OK and out.umax == out.umax
     cav.close()
