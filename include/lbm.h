@@ -132,6 +132,16 @@ int lbm_init(const lbm_params* p, void* stream, lbm_handle* out);
  * Errors: LBM_ERR_ARG, LBM_ERR_STATE (use_phi_field = 0), LBM_ERR_CUDA. */
 int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype);
 
+/* Bounds-checked build (the library compiled with LBM_BOUNDS_CHECK; no
+ * counterpart in the paper): every population, frame and porosity access of
+ * the step kernels' pull, wall rule and stores is checked against its plane
+ * before it is made, and one outside is skipped and counted.  *enabled
+ * (may be NULL) tells whether this library is such a build; *count (may be
+ * NULL) receives the number of skipped accesses on the current device since
+ * the previous call (0 in the normal build), which clears it.  Synchronises
+ * the device.  Errors: LBM_ERR_CUDA. */
+int lbm_bounds_check(int* enabled, long* count);
+
 /* Restarts the cavity from the initial state of lbm_init (t = 0), keeping its
  * parameters, porosity field and launch shape; stream-ordered.  Clears the
  * divergence flag.  Errors: LBM_ERR_ARG (NULL), LBM_ERR_CUDA. */
@@ -188,11 +198,15 @@ int lbm_step_nusselt(lbm_handle h, long nsteps, double* out);
  * one lattice every ckpt_every steps, evaluates J = mean Nu of the hot wall
  * (Eq. 38) at t = nsteps, then sweeps backwards, recomputing each segment of
  * ckpt_every states from its checkpoint, and writes dJ/dphi for every cell
- * (ny*nx dense device values, double for LBM_F64, float for LBM_F32) to
- * dJdphi_dev; *J (host, may be NULL) receives J.  The porosity enters through
- * the per-cell Ergun drag (Eq. 4-5) and the equilibria (Eq. 14, 16, 19, 23).
- * The handle ends at t = nsteps.  Needs use_phi_field = 1, LBM_F64 or LBM_F32,
- * first-order adiabatic walls.  Allocates (nsteps/ckpt_every + ckpt_every + 2)
+ * (ny*nx dense device values, double for LBM_F64, float for the FP32
+ * variants) to dJdphi_dev; *J (host, may be NULL) receives J.  The porosity
+ * enters through the per-cell Ergun drag (Eq. 4-5) and the equilibria (Eq.
+ * 14, 16, 19, 23).  The adjoint is taken at the plain deviations: the
+ * temperature frames of the FP32 storage are an exact change of variables.
+ * The recomputation of each segment runs on a stream of its own, beside the
+ * reverse sweep of the segment after it.  The handle ends at t = nsteps.
+ * Needs use_phi_field = 1, LBM_F64, LBM_F32 or LBM_F32_FRAMED, first-order
+ * adiabatic walls.  Allocates (nsteps/ckpt_every + 2 ckpt_every + 1)
  * lattices of temporary device memory for the call.  Synchronises.
  * Errors: LBM_ERR_STATE (no porosity field), LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void* dJdphi_dev);

@@ -50,6 +50,7 @@ SIGNATURES = [
     ("lbm_set_porous_field", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lbm_step", C.c_int, [C.c_void_p, C.c_long]),
     ("lbm_reset", C.c_int, [C.c_void_p]),
+    ("lbm_bounds_check", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_long)]),
     ("lbm_tune", C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("lbm_observables", C.c_int, [C.c_void_p, C.POINTER(Obs), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_adjoint_step", C.c_int, [C.c_void_p, C.c_long, C.c_long, C.POINTER(C.c_double), C.c_void_p]),

@@ -207,6 +207,36 @@ struct RingStream {
     }
 };
 
+// Third stream for the recomputation of the next segment, with an event per
+// half of the segment storage for "recomputed" and for "read by the reverse
+// sweep" (both recorded once at the start, so the first waits pass).
+struct RecomputeStream {
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, free[2] = {nullptr, nullptr}, end = nullptr;
+    cudaError_t init(cudaStream_t main) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&free[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(free[k], main);  // after the set-up on the main stream
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&end, cudaEventDisableTiming);
+        return e;
+    }
+    // an event behind all recompute work (the main stream waits for it before it returns)
+    cudaEvent_t done() {
+        return cudaEventRecord(end, s3) == cudaSuccess ? end : ready[0];
+    }
+    ~RecomputeStream() {
+        if (end) cudaEventDestroy(end);
+        for (int k = 0; k < 2; ++k) {
+            if (ready[k]) cudaEventDestroy(ready[k]);
+            if (free[k]) cudaEventDestroy(free[k]);
+        }
+        if (s3) cudaStreamDestroy(s3);
+    }
+};
+
 template <class T>
 cudaError_t adjoint_sweep(const AdjointJob& J) {
     using R = typename T::R;
@@ -237,40 +267,54 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
     // Within a reverse step the ring and interior nodes are independent (each
     // writes its own nodes of M^(k) and gphi), so the ring kernel runs on a
     // second stream beside the interior kernel; the main stream waits for it
-    // before the next step and before a recompute overwrites the slots.
+    // before the next step.  The recomputation of a segment needs only its
+    // checkpoint, so it runs on a third stream into the other half of the
+    // segment storage while the main stream reverses the segment after it:
+    // the latency-bound forward steps and reverse steps overlap.
     RingStream rs;
     if ((e = rs.init()) != cudaSuccess) return e;
     auto join = [&]() { return cudaStreamWaitEvent(s, rs.ring_done, 0); };
     if ((e = cudaEventRecord(rs.ring_done, rs.s2)) != cudaSuccess) return e;  // nothing pending on s2 yet
-    int a = 0;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-        const int j0 = sg * K, len = (N - j0) < K ? (N - j0) : K;
-        // slot 0 is the checkpoint; recompute slots 1..len-1 with the forward step
-        std::vector<const void*> slot(len);
-        slot[0] = (const char*)J.ckpt + (size_t)sg * buf;
-        for (int m = 1; m < len; ++m) {
-            void* dst = (char*)J.seg + (size_t)(m - 1) * buf;
+    RecomputeStream rc;
+    if ((e = rc.init(s)) != cudaSuccess) return e;
+    CoefSet cs;
+    if (sizeof(R) == 8) cs.d = *(const Coef<double>*)J.coef;
+    else cs.f = *(const Coef<float>*)J.coef;
+    const size_t half = (size_t)(K > 1 ? K - 1 : 0) * buf;  // bytes of one half of the segment storage
+    auto seg_len = [&](int sg) { return (N - sg * K) < K ? (N - sg * K) : K; };
+    auto slot_of = [&](int sg, int hf, int m) -> const void* {
+        return m == 0 ? (const char*)J.ckpt + (size_t)sg * buf : (const char*)J.seg + hf * half + (size_t)(m - 1) * buf;
+    };
+    // recompute segment sg into half hf on the third stream, once the reverse
+    // sweep that last read that half is done
+    auto recompute = [&](int sg, int hf) -> cudaError_t {
+        cudaError_t er = cudaStreamWaitEvent(rc.s3, rc.free[hf], 0);
+        for (int m = 1; m < seg_len(sg) && er == cudaSuccess; ++m) {
             StepLaunch L;
             L.precision = J.precision;
-            L.src = slot[m - 1];
-            L.dst = dst;
+            L.src = slot_of(sg, hf, m - 1);
+            L.dst = (void*)slot_of(sg, hf, m);
             L.phi = J.phi;
             L.gm = gm;
             L.bx = J.bx;
             L.by = J.by;
             L.npt = J.npt;
             L.status = J.status;
-            L.stream = s;
+            L.stream = rc.s3;
             L.pdl = m > 1;  // directly behind the previous recomputing step
-            CoefSet cs;
-            if (sizeof(R) == 8) cs.d = *(const Coef<double>*)J.coef;
-            else cs.f = *(const Coef<float>*)J.coef;
-            if ((e = launch_step(L, cs)) != cudaSuccess) break;
-            slot[m] = dst;
+            er = launch_step(L, cs);
         }
-        if (e != cudaSuccess) break;
+        if (er == cudaSuccess) er = cudaEventRecord(rc.ready[hf], rc.s3);
+        return er;
+    };
+    int a = 0, hf = 0;
+    e = recompute(nseg - 1, 0);
+    for (int sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg, hf ^= 1) {
+        const int j0 = sg * K, len = seg_len(sg);
+        if (sg > 0 && (e = recompute(sg - 1, hf ^ 1)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(s, rc.ready[hf], 0)) != cudaSuccess) break;
         for (int j = j0 + len - 1; j >= j0; --j) {
-            const Src<T> st = src_view<T>(slot[j - j0], gm.plane);
+            const Src<T> st = src_view<T>(slot_of(sg, hf, j - j0), gm.plane);
             // main_done: everything before this step (previous step, recompute) has finished on s
             if ((e = cudaEventRecord(rs.main_done, s)) != cudaSuccess) break;
             if ((e = cudaStreamWaitEvent(rs.s2, rs.main_done, 0)) != cudaSuccess) break;
@@ -283,8 +327,10 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
             if ((e = join()) != cudaSuccess) break;
             a ^= 1;
         }
-        if (e != cudaSuccess) break;
+        // the half is free again once this segment's reverse sweep is done
+        if (e == cudaSuccess) e = cudaEventRecord(rc.free[hf], s);
     }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, rc.done(), 0);
     if (e != cudaSuccess) {
         (void)join();  // leave no ring work behind the main stream's back
         return e;

@@ -180,8 +180,25 @@ void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
 
 }  // namespace
 
+#ifdef LBM_BOUNDS_CHECK
+// Bounds-checked build: the count of skipped out-of-plane accesses of every
+// kernel of this process on this device (the symbol's device address is
+// looked up on the host, so that nothing is allocated for it).
+__device__ int g_oob_count;
+#endif
+
 namespace lbm {
 void set_global_error(const std::string& msg) { g_init_error = msg; }
+
+int* oob_counter() {
+#ifdef LBM_BOUNDS_CHECK
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_oob_count) != cudaSuccess) return nullptr;
+    return (int*)p;
+#else
+    return nullptr;
+#endif
+}
 
 int setup_lattice(const lbm_params* p, Derived* dv, CoefSet* cs, Geom* gm, std::string* why) {
     int rc = derive(p, dv, why);
@@ -198,6 +215,10 @@ int setup_lattice(const lbm_params* p, Derived* dv, CoefSet* cs, Geom* gm, std::
     gm->plane = (int)plane;
     gm->thermal_bc = p->thermal_bc;
     gm->adi_order = p->adiabatic_order;
+#ifdef LBM_BOUNDS_CHECK
+    gm->oob = oob_counter();
+    if (!gm->oob) return *why = "bounds-checked build: no device counter", LBM_ERR_CUDA;
+#endif
     fill_coef<double>(p, *dv, &cs->d);
     fill_coef<float>(p, *dv, &cs->f);
     return LBM_OK;
@@ -246,6 +267,18 @@ StepLaunch step_launch(lbm_handle h, int src, cudaStream_t s) {
     L.status = h->status_dev;
     L.stream = s;
     return L;
+}
+
+// nsteps steps from buf[cur] in the handle's launch shape, the first launched
+// as a programmatic dependent when pdl_first (a step kernel right before it).
+int advance(lbm_handle h, long nsteps, bool pdl_first) {
+    for (long k = 0; k < nsteps; ++k) {
+        StepLaunch Ls = step_launch(h, h->cur, h->stream);
+        Ls.pdl = k > 0 || pdl_first;
+        CK(h, launch_step(Ls, h->coef));
+        h->cur ^= 1;
+    }
+    return LBM_OK;
 }
 
 // State B_{-1} = rest everywhere (zero deviations) in both buffers, then one
@@ -483,6 +516,24 @@ int lbm_set_porous_field(lbm_handle h, const void* phi_dev, int dtype) {
     return reset_state(h);
 }
 
+int lbm_bounds_check(int* enabled, long* count) {
+#ifdef LBM_BOUNDS_CHECK
+    if (enabled) *enabled = 1;
+    int* p = oob_counter();
+    if (!p) return fail(nullptr, LBM_ERR_CUDA, "bounds-checked build: no device counter");
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof v);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("bounds counter: ") + cudaGetErrorString(e));
+    if (count) *count = v;
+#else
+    if (enabled) *enabled = 0;
+    if (count) *count = 0;
+#endif
+    return LBM_OK;
+}
+
 int lbm_reset(lbm_handle h) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     return reset_state(h);
@@ -532,15 +583,10 @@ int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, i
             h->bx = cd[0];
             h->by = cd[1];
             h->npt = cd[2];
-            for (int k = 0; k < 3; ++k) {
-                CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
-                h->cur ^= 1;
-            }
+            int rc = advance(h, 3, false);
+            if (rc != LBM_OK) return rc;
             CK(h, cudaEventRecord(e0, h->stream));
-            for (int k = 0; k < 30; ++k) {
-                CK(h, launch_step(step_launch(h, h->cur, h->stream), h->coef));
-                h->cur ^= 1;
-            }
+            if ((rc = advance(h, 30, false)) != LBM_OK) return rc;
             CK(h, cudaEventRecord(e1, h->stream));
             CK(h, cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -796,7 +842,8 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
         if (gphi) cudaFree(gphi);
     };
     cudaError_t e = cudaMalloc(&ckpt, (size_t)nseg * h->buf_bytes);
-    if (e == cudaSuccess && K > 1) e = cudaMalloc(&seg, (size_t)(K - 1) * h->buf_bytes);
+    // two halves of K - 1 recomputed states: one segment is recomputed while the next is reversed
+    if (e == cudaSuccess && K > 1) e = cudaMalloc(&seg, 2 * (size_t)(K - 1) * h->buf_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&madj, 2 * (size_t)h->gm.plane * NPOP * rsz);
     if (e == cudaSuccess) e = cudaMalloc(&gphi, sizeof(double) * (size_t)h->p.nx * h->p.ny);
     if (e != cudaSuccess) {
@@ -807,19 +854,23 @@ int lbm_adjoint_step(lbm_handle h, long nsteps, long ckpt_every, double* J, void
     int rc = reset_state(h);
     if (rc == LBM_OK) {
         e = cudaMemsetAsync(ckpt, 0, h->buf_bytes, h->stream);  // j = 0: the rest state B_{-1}
-        for (long t = 0; t < N && e == cudaSuccess; ++t) {
-            const long j = t + 1;  // buf[cur] holds B_t, state index j
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint forward sweep");
+        // runs of steps between the kept states: before step t (buf[cur] holds
+        // B_t, state index j = t + 1) the state is kept when j % K == 0, j < N
+        for (long t = 0; t < N && rc == LBM_OK;) {
+            const long j = t + 1;
             const bool copy = j % K == 0 && j <= N - 1;
-            if (copy)
-                e = cudaMemcpyAsync((char*)ckpt + (size_t)(j / K) * h->buf_bytes, h->buf[h->cur], h->buf_bytes,
-                                    cudaMemcpyDeviceToDevice, h->stream);
-            StepLaunch Ls = step_launch(h, h->cur, h->stream);
-            Ls.pdl = t > 0 && !copy;  // directly behind the previous step kernel
-            if (e == cudaSuccess) e = launch_step(Ls, h->coef);
-            h->cur ^= 1;
+            if (copy && (e = cudaMemcpyAsync((char*)ckpt + (size_t)(j / K) * h->buf_bytes, h->buf[h->cur],
+                                             h->buf_bytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess) {
+                rc = cuda_fail(h, e, "adjoint forward sweep");
+                break;
+            }
+            const long next = (j / K + 1) * K - 1;  // the next step that keeps its input state
+            const long upto = next <= N - 2 ? next : N;
+            rc = advance(h, upto - t, t > 0 && !copy);  // directly behind the previous step kernel
+            t = upto;
         }
         h->t = N;
-        if (e != cudaSuccess) rc = cuda_fail(h, e, "adjoint forward sweep");
     }
     if (rc == LBM_OK) {
         double nuh = 0.0;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "lbm_sync.cuh"
 
 using namespace lbm;
 
@@ -31,44 +32,6 @@ template <class R> struct CavDesc {
 struct Tile {
     int cav, x0, y0;
 };
-
-// Bounded sense-reversing grid barrier.  Thread 0 of each block arrives on
-// count; the last arrival resets count and bumps gen; the others wait for gen
-// to change, at most `limit` polls (sleeps growing from 32 ns to 1 us).  Returns false (in every
-// thread of the block) when the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
-                                             long long limit, int* flag, int* reset_on_release) {
-    __shared__ int ok_sh;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(count, 0u);
-            if (reset_on_release) atomicExch(reset_on_release, 0);
-            __threadfence();
-            atomicAdd((unsigned*)gen, 1u);
-        } else {
-            long long polls = 0;
-            unsigned ns = 32;  // exponential back-off keeps thousands of pollers off the L2 slice
-            while (*gen == g) {
-                if (++polls > limit) {
-                    ok = 0;
-                    atomicOr(flag, 1);
-                    break;
-                }
-                __nanosleep(ns);
-                ns = ns < 1024 ? 2 * ns : 1024;
-            }
-        }
-        __threadfence();
-        ok_sh = ok;
-    }
-    __syncthreads();
-    return ok_sh != 0;
-}
 
 // Node j of a tile.  lg_tw >= 0: a 2^lg_tw-wide rectangle at (x0, y0), row
 // by row; lg_tw < 0: a run of consecutive nodes in the cavity's row-major
@@ -113,11 +76,23 @@ __host__ __device__ __forceinline__ Coef<R> with_cavity_rates(const Coef<R>& cu,
     return c;
 }
 
-// One tile of one step: tiles hold blockDim.x * NPT nodes.
+// One tile of one step: tiles hold blockDim.x * NPT nodes (NPT = 3: two
+// nodes side by side along x per thread, a run of blockDim.x node pairs in
+// the row-major order of the cavity's pairs (x0 even), wrapping onto the next
+// rows; a row of odd width ends in a single node).
 template <class T, int NPT>
 __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
                                             const Dst<T>& dst, const Tile& tl, int lg_tw, int* status) {
-    if constexpr (NPT == 2) {
+    if constexpr (NPT == 3) {
+        const int npx = (gm.nx + 1) >> 1;
+        int xp = (tl.x0 >> 1) + (int)threadIdx.x, y = tl.y0;
+        if (xp >= npx) {
+            const int q = xp / npx;
+            y += q;
+            xp -= q * npx;
+        }
+        if (y < gm.ny) update_xpair<T, false>(c, gm, src, dst, nullptr, 2 * xp, y, status);
+    } else if constexpr (NPT == 2) {
         int x0, y0, x1, y1;
         tile_node(tl, lg_tw, threadIdx.x, gm.nx, x0, y0);
         tile_node(tl, lg_tw, threadIdx.x + blockDim.x, gm.nx, x1, y1);
@@ -345,11 +320,12 @@ struct TuneChoice {
     int tw = 128, th = 2, blocks_per_sm = 0, dyn = 0;
 };
 
-int tile_nodes(const TuneChoice& t) { return t.th == 0 ? t.tw : t.tw * t.th; }
+// th = -1: runs of tw node pairs (two nodes side by side along x per thread)
+int tile_nodes(const TuneChoice& t) { return t.th == -1 ? 2 * t.tw : (t.th == 0 ? t.tw : t.tw * t.th); }
 
 // Tiles of 256 or 512 nodes run with 256-thread blocks; tiles of 32 or 64
 // nodes with one-warp blocks, whose block synchronisation is a warp's.
-int block_of(const TuneChoice& t) { return tile_nodes(t) >= 256 ? 256 : 32; }
+int block_of(const TuneChoice& t) { return t.th == -1 ? t.tw : (tile_nodes(t) >= 256 ? 256 : 32); }
 
 }  // namespace
 
@@ -404,7 +380,8 @@ int bfail(lbm_batch b, int code, const std::string& m) {
     } while (0)
 
 template <class T, bool SPLIT> const void* kernel_ptr(int npt) {
-    return npt == 2 ? (const void*)&k_batch<T, 2, SPLIT> : (const void*)&k_batch<T, 1, SPLIT>;
+    return npt == 3 ? (const void*)&k_batch<T, 3, SPLIT>
+                    : (npt == 2 ? (const void*)&k_batch<T, 2, SPLIT> : (const void*)&k_batch<T, 1, SPLIT>);
 }
 
 // FP64 keeps every coefficient in the descriptor: with the split its
@@ -416,7 +393,7 @@ const void* batch_kernel(int precision, int npt, bool split) {
     return split ? kernel_ptr<PrecF32QP, true>(npt) : kernel_ptr<PrecF32QP, false>(npt);
 }
 
-int npt_of(const TuneChoice& t) { return tile_nodes(t) == 2 * block_of(t) ? 2 : 1; }
+int npt_of(const TuneChoice& t) { return t.th == -1 ? 3 : (tile_nodes(t) == 2 * block_of(t) ? 2 : 1); }
 
 int log2i(int v) {
     int l = 0;
@@ -432,7 +409,13 @@ int build_tiles(lbm_batch b) {
     b->cav_tiles.assign(b->ncav, 0);
     for (int c = 0; c < b->ncav; ++c) {
         const int nx = b->gm[c].nx, ny = b->gm[c].ny;
-        if (b->tune.th == 0) {
+        if (b->tune.th == -1) {
+            const long npx = (nx + 1) / 2;
+            for (long p0 = 0; p0 < npx * ny; p0 += b->tune.tw) {
+                tl.push_back(Tile{c, (int)(2 * (p0 % npx)), (int)(p0 / npx)});
+                ++b->cav_tiles[c];
+            }
+        } else if (b->tune.th == 0) {
             for (long k0 = 0; k0 < (long)nx * ny; k0 += b->tune.tw) {
                 tl.push_back(Tile{c, (int)(k0 % nx), (int)(k0 / nx)});
                 ++b->cav_tiles[c];
@@ -473,7 +456,7 @@ int launch(lbm_batch b, long nsteps, int par, cudaStream_t s) {
     unsigned* cnt = b->bar;
     unsigned* gen = b->bar + 1;
     long long lim = b->wait_limit;
-    int lg = b->tune.th == 0 ? -1 : log2i(b->tune.tw), nt = b->ntiles;
+    int lg = b->tune.th <= 0 ? -1 : log2i(b->tune.tw), nt = b->ntiles;
     const void* descs = b->descs;
     const Tile* tiles = b->tiles;
     int dyn = b->tune.dyn;
@@ -782,7 +765,8 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     bool cached = cache_path && cache_lookup(cache_path, b->signature, &best);
     if (!cached) {
         const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1},
-                                 {32, 1}, {32, 2}, {64, 1}, {32, 0}, {64, 0}, {256, 0}, {512, 0}};
+                                 {32, 1}, {32, 2}, {64, 1}, {32, 0}, {64, 0}, {256, 0}, {512, 0},
+                                 {32, -1}, {64, -1}, {128, -1}, {256, -1}};
         const int occ[] = {0, 2};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -832,10 +816,13 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     const int tn = tile_h == 0 ? tile_w : tile_w * tile_h;
-    if (tile_w <= 0 || tile_h < 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
-        (tile_h > 0 && ((tile_w & (tile_w - 1)) != 0 || tile_w < 32)) || blocks_per_sm < 0)
+    const bool pairs = tile_h == -1 && (tile_w == 32 || tile_w == 64 || tile_w == 128 || tile_w == 256);
+    if (!pairs && (tile_w <= 0 || tile_h < 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
+                   (tile_h > 0 && ((tile_w & (tile_w - 1)) != 0 || tile_w < 32)) || blocks_per_sm < 0))
         return bfail(b, LBM_ERR_ARG, "tiles hold 32, 64, 256 or 512 nodes: a power-of-two width >= 32 times "
-                                     "tile_h rows, or tile_h = 0 for runs of tile_w consecutive nodes");
+                                     "tile_h rows, tile_h = 0 for runs of tile_w consecutive nodes, or "
+                                     "tile_h = -1 for runs of tile_w (32 to 256) node pairs");
+    if (blocks_per_sm < 0) return bfail(b, LBM_ERR_ARG, "blocks_per_sm < 0");
     b->tune.tw = tile_w;
     b->tune.th = tile_h;
     b->tune.blocks_per_sm = blocks_per_sm;

@@ -268,7 +268,25 @@ struct Geom {
     int plane;        // elements per population plane (pitch * ny)
     int thermal_bc;   // 0 side-heated, 1 cooled
     int adi_order;    // 1 or 2
+#ifdef LBM_BOUNDS_CHECK
+    int* oob;         // counter of accesses outside their plane (bounds-checked build)
+#endif
 };
+
+// Bounds-checked build (LBM_BOUNDS_CHECK): every population, frame and
+// porosity access of the step's pull, wall rule and stores is checked against
+// its plane [0, plane) first; an access outside it is skipped (a load reads 0)
+// and counted in *gm.oob.  In the normal build the check is compiled away.
+__device__ __forceinline__ bool in_plane(const Geom& gm, int o, int n = 1) {
+#ifdef LBM_BOUNDS_CHECK
+    if (o >= 0 && o <= gm.plane - n) return true;
+    atomicAdd(gm.oob, 1);
+    return false;
+#else
+    (void)gm, (void)o, (void)n;
+    return true;
+#endif
+}
 
 // Porosity-dependent drag coefficients (Eq. 4 and Eq. 5 per cell).
 template <class R> struct Drag {
@@ -299,6 +317,11 @@ __device__ __forceinline__ Drag<R> drag_of(const Coef<R>& c, R phi) {
 template <class R, bool FIELD, class P>
 __device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const P* phi_field, int off) {
     if constexpr (FIELD) return drag_of<R, true>(c, Conv<P, R>::ld(phi_field + off));
+    return drag_of<R, false>(c, R(0));
+}
+template <class R, bool FIELD, class P>
+__device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const Geom& gm, const P* phi_field, int off) {
+    if constexpr (FIELD) return drag_at<R, FIELD, P>(c, phi_field, in_plane(gm, off) ? off : 0);
     return drag_of<R, false>(c, R(0));
 }
 
@@ -361,11 +384,15 @@ __device__ __forceinline__ void pull(const Src<T>& src, const Geom& gm, int off,
                                      typename T::R (&d)[9], typename T::R (&h)[5]) {
     using R = typename T::R;
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        d[i] = Conv<typename T::SF, R, T::cg>::ld(src.f + i * gm.plane + off - ey9(i) * gm.pitch - ex9(i));
+    for (int i = 0; i < 9; ++i) {
+        const int o = off - ey9(i) * gm.pitch - ex9(i);
+        d[i] = in_plane(gm, o) ? Conv<typename T::SF, R, T::cg>::ld(src.f + i * gm.plane + o) : R(0);
+    }
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
-        h[j] = Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+    for (int j = 0; j < 5; ++j) {
+        const int o = off - ey9(j) * gm.pitch - ex9(j);
+        h[j] = in_plane(gm, o) ? Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + o) : R(0);
+    }
 }
 
 template <class T>
@@ -373,8 +400,10 @@ __device__ __forceinline__ typename T::R pull_heat(const Src<T>& src, const Geom
     using R = typename T::R;
     R t = 0;
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
-        t += Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+    for (int j = 0; j < 5; ++j) {
+        const int o = off - ey9(j) * gm.pitch - ex9(j);
+        t += in_plane(gm, o) ? Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + o) : R(0);
+    }
     return t;
 }
 
@@ -389,26 +418,28 @@ __device__ __forceinline__ void pull_x2(const Src<T>& src, const Geom& gm, int o
     using SG = typename T::SG;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const SF* p = src.f + i * gm.plane + off0 - ey9(i) * gm.pitch - ex9(i);
+        const int o = off0 - ey9(i) * gm.pitch - ex9(i);
+        const SF* p = src.f + i * gm.plane + o;
         if (ex9(i) == 0) {
-            const auto v = Conv2<SF, R, T::cg>::ld(p);
+            const auto v = in_plane(gm, o, 2) ? Conv2<SF, R, T::cg>::ld(p) : decltype(Conv2<SF, R, T::cg>::ld(p)){};
             d0[i] = v.x;
             d1[i] = v.y;
         } else {
-            d0[i] = Conv<SF, R, T::cg>::ld(p);
-            d1[i] = Conv<SF, R, T::cg>::ld(p + 1);
+            d0[i] = in_plane(gm, o) ? Conv<SF, R, T::cg>::ld(p) : R(0);
+            d1[i] = in_plane(gm, o + 1) ? Conv<SF, R, T::cg>::ld(p + 1) : R(0);
         }
     }
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        const SG* p = src.g + j * gm.plane + off0 - ey9(j) * gm.pitch - ex9(j);
+        const int o = off0 - ey9(j) * gm.pitch - ex9(j);
+        const SG* p = src.g + j * gm.plane + o;
         if (ex9(j) == 0) {
-            const auto v = Conv2<SG, R, T::cg>::ld(p);
+            const auto v = in_plane(gm, o, 2) ? Conv2<SG, R, T::cg>::ld(p) : decltype(Conv2<SG, R, T::cg>::ld(p)){};
             h0[j] = v.x;
             h1[j] = v.y;
         } else {
-            h0[j] = Conv<SG, R, T::cg>::ld(p);
-            h1[j] = Conv<SG, R, T::cg>::ld(p + 1);
+            h0[j] = in_plane(gm, o) ? Conv<SG, R, T::cg>::ld(p) : R(0);
+            h1[j] = in_plane(gm, o + 1) ? Conv<SG, R, T::cg>::ld(p + 1) : R(0);
         }
     }
 }
@@ -421,11 +452,13 @@ __device__ __forceinline__ void frame_in_x2(const Coef<typename T::R>& c, const 
                                             int off0, typename T::R (&h0)[5], typename T::R (&h1)[5],
                                             typename T::R& F0, typename T::R& F1) {
     using R = typename T::R;
-    R n0, n1, s0, s1;
-    frame_ld2<T>(c, src.t + off0, F0, F1);
-    frame_ld2<T>(c, src.t + off0 - gm.pitch, s0, s1);  // j = 2 pulls from y - 1
-    frame_ld2<T>(c, src.t + off0 + gm.pitch, n0, n1);  // j = 4 pulls from y + 1
-    const R w = frame_ld<T>(c, src.t + off0 - 1), e = frame_ld<T>(c, src.t + off0 + 2);
+    R n0 = R(0), n1 = R(0), s0 = R(0), s1 = R(0), w = R(0), e = R(0);
+    F0 = F1 = R(0);
+    if (in_plane(gm, off0, 2)) frame_ld2<T>(c, src.t + off0, F0, F1);
+    if (in_plane(gm, off0 - gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 - gm.pitch, s0, s1);  // j = 2: from y - 1
+    if (in_plane(gm, off0 + gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 + gm.pitch, n0, n1);  // j = 4: from y + 1
+    if (in_plane(gm, off0 - 1)) w = frame_ld<T>(c, src.t + off0 - 1);
+    if (in_plane(gm, off0 + 2)) e = frame_ld<T>(c, src.t + off0 + 2);
     h0[1] += c.wt1 * (w - F0);
     h1[1] += c.wt1 * (F0 - F1);
     h0[2] += c.wt1 * (s0 - F0);
@@ -444,9 +477,12 @@ template <class T>
 __device__ __forceinline__ typename T::R frame_in(const Coef<typename T::R>& c, const Src<T>& src, const Geom& gm,
                                                   int off, typename T::R (&h)[5]) {
     using R = typename T::R;
-    const R F = frame_ld<T>(c, src.t + off);
+    const R F = in_plane(gm, off) ? frame_ld<T>(c, src.t + off) : R(0);
 #pragma unroll
-    for (int j = 1; j < 5; ++j) h[j] += c.wt1 * (frame_ld<T>(c, src.t + off - ey9(j) * gm.pitch - ex9(j)) - F);
+    for (int j = 1; j < 5; ++j) {
+        const int o = off - ey9(j) * gm.pitch - ex9(j);
+        h[j] += c.wt1 * ((in_plane(gm, o) ? frame_ld<T>(c, src.t + o) : R(0)) - F);
+    }
     return F;
 }
 
@@ -457,8 +493,10 @@ __device__ __forceinline__ typename T::R pull_heat_framed(const Coef<typename T:
     using R = typename T::R;
     R h[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
-        h[j] = Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + off - ey9(j) * gm.pitch - ex9(j));
+    for (int j = 0; j < 5; ++j) {
+        const int o = off - ey9(j) * gm.pitch - ex9(j);
+        h[j] = in_plane(gm, o) ? Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + o) : R(0);
+    }
     F = frame_in<T>(c, src, gm, off, h);
     return h[0] + h[1] + h[2] + h[3] + h[4];
 }
@@ -633,9 +671,9 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
     R Ff = R(0), Fb = R(0);  // frames of the inner neighbour and of this wall node
     if constexpr (FR) {
         Ff = frame_in<T>(c, src, gm, offf, hf);
-        Fb = frame_ld<T>(c, src.t + y * gm.pitch + x);
+        Fb = in_plane(gm, y * gm.pitch + x) ? frame_ld<T>(c, src.t + y * gm.pitch + x) : R(0);
     }
-    const Drag<R> drf = drag_at<R, FIELD, typename T::P>(c, phi_field, offf);
+    const Drag<R> drf = drag_at<R, FIELD, typename T::P>(c, gm, phi_field, offf);
     const Macro<R> mf = fluid_macros<R, R, FR>(c, drf, df, hf, Ff);
 
     Macro<R> mb;
@@ -715,7 +753,7 @@ __device__ __forceinline__ Macro<typename T::R> node_state(const Coef<typename T
                                                            typename T::R (&d)[9], typename T::R (&h)[5]) {
     using R = typename T::R;
     const int off = y * gm.pitch + x;
-    dr = drag_at<R, FIELD, typename T::P>(c, phi_field, off);
+    dr = drag_at<R, FIELD, typename T::P>(c, gm, phi_field, off);
     const Normal nr = normal_of(gm, x, y);
     if (nr.dx == 0 && nr.dy == 0) {
         pull<T>(src, gm, off, d, h);
@@ -741,7 +779,7 @@ __device__ __forceinline__ void frame_out(const Coef<typename T::R>& c, const Ge
     h[0] -= c.wt0 * shift;
 #pragma unroll
     for (int j = 1; j < 5; ++j) h[j] -= c.wt1 * shift;
-    dst.t[off] = code;
+    if (in_plane(gm, off)) dst.t[off] = code;
 }
 
 // ---- wall-column temperatures -------------------------------------------------------
@@ -784,10 +822,12 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     collide<R, R, Framed<T>::value>(c, dr.iphi, mc, d, h);
     const int off = y * gm.pitch + x;
     if constexpr (Framed<T>::value) frame_out<T>(c, gm, dst, off, mc, h);
+    if (in_plane(gm, off)) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
+        for (int i = 0; i < 9; ++i) Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off, d[i]);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+        for (int j = 0; j < 5; ++j) Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off, h[j]);
+    }
     if constexpr (OBS) obs_put(gm, obs, x, y, obs_value<T>(mc));
 }
 
@@ -828,27 +868,33 @@ __device__ __forceinline__ void collide_fluid_pair_x2(const Coef<float>& c, cons
 #pragma unroll
         for (int j = 1; j < 5; ++j) h[j] = h[j] - c.wt1 * sh;
         if constexpr (VEC) {
-            frame_st2<T>(dst.t + off0, k0, k1);
+            if (in_plane(gm, off0, 2)) frame_st2<T>(dst.t + off0, k0, k1);
         } else {
-            dst.t[off0] = k0;
-            dst.t[off1] = k1;
+            if (in_plane(gm, off0)) dst.t[off0] = k0;
+            if (in_plane(gm, off1)) dst.t[off1] = k1;
         }
     }
     if constexpr (VEC) {
+        if (in_plane(gm, off0, 2)) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Conv2<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off0, d[i].v.x, d[i].v.y);
+            for (int i = 0; i < 9; ++i)
+                Conv2<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off0, d[i].v.x, d[i].v.y);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) Conv2<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x, h[j].v.y);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off0, d[i].v.x);
-            Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off1, d[i].v.y);
+            for (int j = 0; j < 5; ++j)
+                Conv2<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x, h[j].v.y);
         }
+    } else {
+        if (in_plane(gm, off0)) {
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x);
-            Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off1, h[j].v.y);
+            for (int i = 0; i < 9; ++i) Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off0, d[i].v.x);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off0, h[j].v.x);
+        }
+        if (in_plane(gm, off1)) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Conv<typename T::SF, float, T::cg>::st(dst.f + i * gm.plane + off1, d[i].v.y);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) Conv<typename T::SG, float, T::cg>::st(dst.g + j * gm.plane + off1, h[j].v.y);
         }
     }
     if constexpr (OBS) {
@@ -876,8 +922,8 @@ __device__ __forceinline__ void update_fluid_pair_x2(const Coef<float>& c, const
         F0 = frame_in<T>(c, src, gm, off0, b0);
         F1 = frame_in<T>(c, src, gm, off1, b1);
     }
-    const Drag<float> r0 = drag_at<float, FIELD, typename T::P>(c, phi, off0);
-    const Drag<float> r1 = drag_at<float, FIELD, typename T::P>(c, phi, off1);
+    const Drag<float> r0 = drag_at<float, FIELD, typename T::P>(c, gm, phi, off0);
+    const Drag<float> r1 = drag_at<float, FIELD, typename T::P>(c, gm, phi, off1);
     collide_fluid_pair_x2<T, OBS>(c, gm, dst, a0, b0, a1, b1, r0, r1, off0, off1, status, x0, y0, x1, y1, obs, F0,
                                   F1);
 }
@@ -909,8 +955,8 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
             F0 = frame_in<T>(c, src, gm, off0, h0);
             F1 = frame_in<T>(c, src, gm, off1, h1);
         }
-        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
-        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
+        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off0);
+        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off1);
         const Macro<R> m0 = fluid_macros<R, R, FR>(c, dr0, d0, h0, F0);
         const Macro<R> m1 = fluid_macros<R, R, FR>(c, dr1, d1, h1, F1);
         if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
@@ -920,15 +966,17 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
             frame_out<T>(c, gm, dst, off0, m0, h0);
             frame_out<T>(c, gm, dst, off1, m1, h1);
         }
+        if (in_plane(gm, off0) && in_plane(gm, off1)) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
-            Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off1, d1[i]);
-        }
+            for (int i = 0; i < 9; ++i) {
+                Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i]);
+                Conv<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off1, d1[i]);
+            }
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
-            Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
+            for (int j = 0; j < 5; ++j) {
+                Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j]);
+                Conv<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off1, h1[j]);
+            }
         }
         if constexpr (OBS) {
             obs_put(gm, obs, x0, y0, obs_value<T>(m0));
@@ -957,8 +1005,8 @@ __device__ __forceinline__ void update_xpair(const Coef<typename T::R>& c, const
         pull_x2<T>(src, gm, off0, d0, h0, d1, h1);
         R F0 = R(0), F1 = R(0);
         if constexpr (FR) frame_in_x2<T>(c, src, gm, off0, h0, h1, F0, F1);
-        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, phi, off0);
-        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, phi, off1);
+        const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off0);
+        const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off1);
         if constexpr (Paired<T>::value) {
             collide_fluid_pair_x2<T, OBS, true>(c, gm, dst, d0, h0, d1, h1, dr0, dr1, off0, off1, status, x0, y, x1,
                                                 y, obs, F0, F1);
@@ -979,12 +1027,16 @@ __device__ __forceinline__ void update_xpair(const Coef<typename T::R>& c, const
                     h0[j] -= c.wt1 * s0;
                     h1[j] -= c.wt1 * s1;
                 }
-                frame_st2<T>(dst.t + off0, k0, k1);
+                if (in_plane(gm, off0, 2)) frame_st2<T>(dst.t + off0, k0, k1);
             }
+            if (in_plane(gm, off0, 2)) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Conv2<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i], d1[i]);
+                for (int i = 0; i < 9; ++i)
+                    Conv2<typename T::SF, R, T::cg>::st(dst.f + i * gm.plane + off0, d0[i], d1[i]);
 #pragma unroll
-            for (int j = 0; j < 5; ++j) Conv2<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j], h1[j]);
+                for (int j = 0; j < 5; ++j)
+                    Conv2<typename T::SG, R, T::cg>::st(dst.g + j * gm.plane + off0, h0[j], h1[j]);
+            }
             if constexpr (OBS) {
                 obs_put(gm, obs, x0, y, obs_value<T>(m0));
                 obs_put(gm, obs, x1, y, obs_value<T>(m1));

@@ -49,6 +49,10 @@ inline bool ckpt_layout_current(int version, int precision) {
     return version == 3 || precision == LBM_F64 || precision == LBM_F32_FRAMED;
 }
 
+// Bounds-checked build: device address of the out-of-plane access counter
+// (nullptr in the normal build).
+int* oob_counter();
+
 // Error text returned by lbm_last_error(NULL) (calls without a handle).
 void set_global_error(const std::string& msg);
 
@@ -110,8 +114,8 @@ cudaError_t launch_nusselt(const ObserveLaunch& L, const CoefSet& cs);
 cudaError_t launch_read_state(const ReadStateLaunch& L, const CoefSet& cs);
 // One reverse sweep of the discrete adjoint (lbm_adjoint.cu).  ckpt holds the
 // states B_{sK-1} for every segment s (slot 0: the rest state), seg has room
-// for K - 1 recomputed states, madj for two adjoint lattices (14 planes in the
-// arithmetic type), gphi one double per node.
+// for 2 (K - 1) recomputed states (two segments), madj for two adjoint
+// lattices (14 planes in the arithmetic type), gphi one double per node.
 struct AdjointJob {
     int precision;
     Geom gm;

@@ -139,3 +139,90 @@ def test_autograd_backward_detects_a_changed_cavity(phi):
     with pytest.raises(RuntimeError, match="changed between forward and backward"):
         J.backward()
     cav2.close()
+
+
+# ---- the sizes the gradient benchmark states ------------------------------------------
+
+def _cells_of_every_kind(n):
+    """16 cells on a square n x n cavity: the hot wall, its corners, the adiabatic
+    walls, next to each wall, the interior and the cold wall."""
+    m = n // 2
+    return [(0, m), (0, 0), (0, n - 1), (1, m), (2, m + 3), (m, 0), (m + 5, n - 1), (m, 1), (m - 7, n - 2),
+            (m, m), (n // 4, 3 * n // 4), (3 * n // 4, n // 5), (n - 2, m), (n - 1, m - 4), (n - 1, 0), (1, 1)]
+
+
+def _fd_cells_and_directions(phi, nsteps, nthreads, cells, ndirs, seed):
+    """Central differences of the FP64 oracle's J = Nu_hot(t_N): h = 1e-5 phi at
+    single cells, h = 1e-5 along unit random directions."""
+    n = phi.shape[0]
+
+    def J(p):
+        o = Oracle(derive(n, n, Ra=1e5, Da=1e-2, phi=0.6), phi_field=p).step(nsteps, threads=nthreads)
+        return o.nusselt()[0]
+
+    fd = []
+    for (x, y) in cells:
+        h = 1e-5 * phi[y, x]
+        p = phi.copy()
+        p[y, x] += h
+        jp = J(p)
+        p[y, x] -= 2 * h
+        fd.append((jp - J(p)) / (2 * h))
+    rng = np.random.default_rng(seed)
+    dirs = []
+    for _ in range(ndirs):
+        v = rng.standard_normal(phi.shape)
+        v /= np.linalg.norm(v)
+        fd.append((J(phi + 1e-5 * v) - J(phi - 1e-5 * v)) / 2e-5)
+        dirs.append(v)
+    return np.array(fd), dirs
+
+
+@pytest.fixture(scope="module")
+def fd_64(nthreads):
+    """64^2 cavity of the gradient benchmark's physics (Ra 1e5, Da 1e-2, porosity
+    0.6 plus a smooth perturbation), 2000 steps: 16 cells and 2 directions."""
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    phi = perturbed_porosity(64, 64, phi_bar=0.6, amplitude=0.05, corr_len=8.0, seed=64)
+    cells = _cells_of_every_kind(64)
+    fd, dirs = _fd_cells_and_directions(phi, 2000, nthreads, cells, 2, seed=640)
+    return phi, cells, fd, dirs
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-6), ("f32", 1e-3)])
+def test_adjoint_at_64_squared_matches_oracle_central_differences(fd_64, precision, tol):
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+
+    phi, cells, fd, dirs = fd_64
+    cav = Cavity(64, 64, Ra=1e5, Da=1e-2, phi=0.6, precision=precision, phi_field=torch.from_numpy(phi).cuda())
+    _, g = cav.adjoint(2000, 100)
+    g = g.double().cpu().numpy()
+    ad = np.array([g[y, x] for (x, y) in cells] + [float((g * v).sum()) for v in dirs])
+    err = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
+    assert err < tol, (precision, err, list(zip(ad, fd)))
+    cav.close()
+
+
+def test_adjoint_at_512_squared_along_random_directions(nthreads):
+    # The gradient benchmark itself: 512^2, 2000 steps, checkpoint every 100,
+    # FP32 storage; its gradient along two random unit directions against
+    # central differences of the FP64 oracle (four oracle runs of 5.2e8 node
+    # updates each).
+    import torch
+
+    from paper_1308_2071_gb300 import Cavity
+    from paper_1308_2071_gb300.inputs import perturbed_porosity
+
+    n = 512
+    phi = perturbed_porosity(n, n, phi_bar=0.6, amplitude=0.05, corr_len=8.0, seed=2000)
+    fd, dirs = _fd_cells_and_directions(phi, 2000, nthreads, [], 2, seed=512)
+    cav = Cavity(n, n, Ra=1e5, Da=1e-2, phi=0.6, precision="f32", phi_field=torch.from_numpy(phi).cuda())
+    _, g = cav.adjoint(2000, 100)
+    g = g.double().cpu().numpy()
+    ad = np.array([float((g * v).sum()) for v in dirs])
+    err = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
+    assert err < 1e-3, (err, list(zip(ad, fd)))
+    cav.close()

@@ -79,8 +79,8 @@ def test_steady_loop_stops_on_divergence():
     cav = Cavity(40, 40, Ra=1e5, Da=1e-2, phi=0.6, precision="f32")
     cav.step(10)
     blob = cav.save()
-    payload = 14 * 64 * 40 * 4
-    arr = np.frombuffer(blob, dtype=np.float32, count=payload // 4, offset=len(blob) - payload)
+    # B_{n-1} after the 40-byte header: 14 float32 planes (row pitch 64), then the frames
+    arr = np.frombuffer(blob, dtype=np.float32, count=14 * 64 * 40, offset=40)
     arr.setflags(write=True)
     arr[20 * 64 + 20] = np.nan
     cav.load(blob)
