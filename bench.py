@@ -66,14 +66,39 @@ def parse():
     return ap.parse_args()
 
 
-def kernel_sources_digest():
+def kernel_sources_digest(names=("lbm_device.cuh", "lbm_kernels.cu")):
     import hashlib
 
     hsh = hashlib.sha256()
-    for name in ("lbm_device.cuh", "lbm_kernels.cu"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1308_2071_gb300", "csrc", name), "rb") as f:
             hsh.update(f.read())
     return hsh.hexdigest()[:16]
+
+
+ADJOINT_SOURCES = ("lbm_device.cuh", "lbm_kernels.cu", "lbm_adjoint.cuh", "lbm_adjoint.cu")
+
+
+def recorded_adjoint_instructions():
+    """Warp instructions per launch of the adjoint's kernels at 512^2 from the
+    committed ncu summary, if the kernel sources are the ones that were
+    measured; else None."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "k_adjoint_f32_512.md")).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":", 1)[0] in ("kernel_sources_sha256", "warp_instructions_k_step2x",
+                                                      "warp_instructions_k_adjoint", "warp_instructions_k_adjoint_ring"):
+            k, v = line.split(":", 1)
+            vals[k] = v.strip()
+    if vals.get("kernel_sources_sha256") != kernel_sources_digest(ADJOINT_SOURCES):
+        return None
+    try:
+        return {k: int(v) for k, v in vals.items() if k.startswith("warp_")}
+    except ValueError:
+        return None
 
 
 def recorded_traffic(precision, n, field=False):
@@ -387,10 +412,12 @@ def batched_leg(steps, warmup, ncav=256, seed=2071):
     q = b.query()
     b.close()
     peak, _ = load_peaks()
-    gbs = nodes * BYTES_PER_NODE["f32"] / (ms * 1e-3 / steps) / 1e9
+    gbs = nodes * BYTES_PER_NODE["f32"] / (ms * 1e-3 / steps) / 1e9  # 114 B per node-step
     return dict(cavities=ncav, nodes=nodes, steps=steps, mlups=round(nodes * steps / (ms * 1e-3) / 1e6, 2),
                 hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / peak, 4), tile=[tw, th], blocks_per_sm=bps,
-                nodes_per_thread=1 if tw * th in (32, 256) else 2,
+                tile_kind=("runs of node pairs side by side along x" if th == -1 else
+                           "runs of consecutive nodes" if th == 0 else "rectangles"),
+                nodes_per_thread=(2 if th == -1 else 1 if (tw if th == 0 else tw * th) in (32, 256) else 2),
                 mode="one persistent cooperative launch per call, graph-captured",
                 blocks=q["nblocks"], tiles=q["ntiles"], launches=1, diverged=int(st.sum()),
                 status=int(rc), sizes="U{64..512} square, seed %d" % seed)
@@ -418,12 +445,36 @@ def adjoint_leg(n=512, nsteps=2000, ckpt=100):
     cav.close()
     mlups = n * n * nsteps / dt / 1e6
     peak, _ = load_peaks()
-    # per node-step: forward recompute 112 B + reverse 56 (state) + 56 (lambda in) + 56 (lambda out)
-    # + 4 (phi) + 8 (dJ/dphi read and write, FP64), about 292 B
-    return dict(workload=f"{n}x{n}, Ra 1e5, Da 1e-2, {nsteps} steps, checkpoint every {ckpt}, FP32",
-                mlups=round(mlups, 2), seconds=round(dt, 3), J=J, grad_l2=float(g.double().norm()),
-                bytes_per_node_step=292, frac_of_hbm=round(mlups * 1e6 * 292 / (peak * 1e9), 4),
-                note="the 512^2 lattice and adjoint state are L2-resident: not HBM-bound, latency-bound")
+    out = dict(workload=f"{n}x{n}, Ra 1e5, Da 1e-2, {nsteps} steps, checkpoint every {ckpt}, FP32",
+               mlups=round(mlups, 2), seconds=round(dt, 3), J=J, grad_l2=float(g.double().norm()))
+    # The lattice (15 MB per state) and the adjoint state stay in L2, so HBM
+    # is not the bound; the kernels are instruction- and latency-bound.  Bound:
+    # the instruction issue rate (4 warp instructions per SM per clock at the
+    # maximum SM clock) over the warp instructions one gradient executes: the
+    # forward sweep and the recomputation (2 N - ceil(N / K) step launches) and
+    # N reverse steps (interior and wall-ring kernels), per launch from ncu.
+    ins = recorded_adjoint_instructions()
+    if ins:
+        nseg = -(-nsteps // ckpt)
+        total = ((2 * nsteps - nseg) * ins["warp_instructions_k_step2x"]
+                 + nsteps * (ins["warp_instructions_k_adjoint"] + ins["warp_instructions_k_adjoint_ring"]))
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+        ipeak = nsm * 4 * mhz * 1e6
+        out["roofline"] = dict(bound="issue", achieved=round(total / dt / 1e9, 1), peak=round(ipeak / 1e9, 1),
+                               unit="G warp instructions/s", frac=round(total / dt / ipeak, 4),
+                               warp_instructions=total, source="ncu smsp__inst_executed.sum per launch, "
+                                                               "profiles/k_adjoint_f32_512.md")
+    else:
+        out["roofline"] = dict(bound="issue", achieved=None, frac=None,
+                               note="no ncu instruction counts recorded for these kernel sources")
+    # HBM fraction for context: per node-step forward recompute 114 B + reverse 56 (state) + 56
+    # (lambda in) + 56 (lambda out) + 4 (phi) + 8 (dJ/dphi read and write, FP64), about 294 B
+    out.update(bytes_per_node_step=294, frac_of_hbm=round(mlups * 1e6 * 294 / (peak * 1e9), 4))
+    return out
 
 
 def heterogeneous_leg(n=8192, steps=1000, warmup=3):

@@ -176,6 +176,7 @@ void fill_coef(const lbm_params* p, const Derived& dv, Coef<R>* c) {
     const double fq = exp2(ceil(log2(tspan / 128.0)));
     c->fq = (R)fq;
     c->ifq = (R)(1.0 / fq);
+    c->wt1fq = (R)((4.0 + p->varpi) / 20.0) * (R)fq;
 }
 
 }  // namespace

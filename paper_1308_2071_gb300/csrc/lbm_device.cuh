@@ -43,20 +43,25 @@ constexpr int NPOP = 14;  // 9 flow + 5 thermal planes per buffer
 
 // ---- storage conversions ------------------------------------------------------
 
-// CG = false: read-only cached loads (the buffer is never written during the
-// launch).  CG = true: loads cached in L2 only, for kernels that read data
-// other blocks of the same launch wrote (the persistent batched kernel).
+// CG = false: read-only (non-coherent) cached loads, for buffers never
+// written during the launch.  CG = true: coherent loads (ld.global.ca), for
+// kernels that read data other blocks of the same launch wrote (the
+// persistent batched kernel): a weak load observes every write that happens
+// before it through the kernel's release/acquire synchronisation (the grid
+// barrier, or the dataflow schedule's wait), and may hit L1, which the
+// neighbouring nodes' shifted pulls and frames reuse; the non-coherent path
+// of __ldg gives no such guarantee within a launch.
 template <class S, class R, bool CG = false> struct Conv;
 template <bool CG> struct Conv<double, double, CG> {
-    static __device__ __forceinline__ double ld(const double* p) { return CG ? __ldcg(p) : __ldg(p); }
+    static __device__ __forceinline__ double ld(const double* p) { return CG ? __ldca(p) : __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <bool CG> struct Conv<float, float, CG> {
-    static __device__ __forceinline__ float ld(const float* p) { return CG ? __ldcg(p) : __ldg(p); }
+    static __device__ __forceinline__ float ld(const float* p) { return CG ? __ldca(p) : __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <bool CG> struct Conv<__half, float, CG> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(CG ? __ldcg(p) : __ldg(p)); }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(CG ? __ldca(p) : __ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -65,19 +70,19 @@ template <bool CG> struct Conv<__half, float, CG> {
 template <class S, class R, bool CG = false> struct Conv2;
 template <bool CG> struct Conv2<double, double, CG> {
     static __device__ __forceinline__ double2 ld(const double* p) {
-        return CG ? __ldcg((const double2*)p) : __ldg((const double2*)p);
+        return CG ? __ldca((const double2*)p) : __ldg((const double2*)p);
     }
     static __device__ __forceinline__ void st(double* p, double a, double b) { *(double2*)p = make_double2(a, b); }
 };
 template <bool CG> struct Conv2<float, float, CG> {
     static __device__ __forceinline__ float2 ld(const float* p) {
-        return CG ? __ldcg((const float2*)p) : __ldg((const float2*)p);
+        return CG ? __ldca((const float2*)p) : __ldg((const float2*)p);
     }
     static __device__ __forceinline__ void st(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
 };
 template <bool CG> struct Conv2<__half, float, CG> {
     static __device__ __forceinline__ float2 ld(const __half* p) {
-        return __half22float2(CG ? __ldcg((const __half2*)p) : __ldg((const __half2*)p));
+        return __half22float2(CG ? __ldca((const __half2*)p) : __ldg((const __half2*)p));
     }
     static __device__ __forceinline__ void st(__half* p, float a, float b) { *(__half2*)p = __floats2half2_rn(a, b); }
 };
@@ -259,6 +264,7 @@ template <class R> struct Coef {
     R a_lin;      // per-cell: phi nu / K      = a_lin  (1 - phi)^2 / phi^2
     R a_quad;     // per-cell: phi F_phi / sqrt K = a_quad (1 - phi) / phi^2
     R fq, ifq;    // 8-bit temperature frames: quantum (a power of two) and its inverse
+    R wt1fq;      // w~_1 fq (exact: fq is a power of two)
 };
 
 // Geometry of one lattice in one pair of buffers.
@@ -331,7 +337,7 @@ __device__ __forceinline__ Drag<R> drag_at(const Coef<R>& c, const Geom& gm, con
 template <class T, class R>
 __device__ __forceinline__ R frame_ld(const Coef<R>& c, const typename FrameStore<T>::type* p) {
     if constexpr (sizeof(typename FrameStore<T>::type) == 1) {
-        const int8_t k = T::cg ? __ldcg((const signed char*)p) : __ldg((const signed char*)p);
+        const int8_t k = T::cg ? __ldca((const signed char*)p) : __ldg((const signed char*)p);
         return R((int)k) * c.fq;
     } else {
         return Conv<typename FrameStore<T>::type, R, T::cg>::ld(p);
@@ -353,11 +359,21 @@ __device__ __forceinline__ R frame_make(const Coef<R>& c, R v, typename FrameSto
     }
 }
 
+// The stored code k of an 8-bit frame (F = k fq), and of a node pair.
+template <class T>
+__device__ __forceinline__ int frame_code(const typename FrameStore<T>::type* p) {
+    return (int)(T::cg ? __ldca((const signed char*)p) : __ldg((const signed char*)p));
+}
+template <class T>
+__device__ __forceinline__ char2 frame_pair_code(const typename FrameStore<T>::type* p) {
+    return T::cg ? __ldca((const char2*)p) : __ldg((const char2*)p);
+}
+
 // Frames of the node pair (x0, x0 + 1), x0 even.
 template <class T, class R>
 __device__ __forceinline__ void frame_ld2(const Coef<R>& c, const typename FrameStore<T>::type* p, R& a, R& b) {
     if constexpr (sizeof(typename FrameStore<T>::type) == 1) {
-        const char2 k = T::cg ? __ldcg((const char2*)p) : __ldg((const char2*)p);
+        const char2 k = T::cg ? __ldca((const char2*)p) : __ldg((const char2*)p);
         a = R((int)(signed char)k.x) * c.fq;
         b = R((int)(signed char)k.y) * c.fq;
     } else {
@@ -452,21 +468,43 @@ __device__ __forceinline__ void frame_in_x2(const Coef<typename T::R>& c, const 
                                             int off0, typename T::R (&h0)[5], typename T::R (&h1)[5],
                                             typename T::R& F0, typename T::R& F1) {
     using R = typename T::R;
-    R n0 = R(0), n1 = R(0), s0 = R(0), s1 = R(0), w = R(0), e = R(0);
-    F0 = F1 = R(0);
-    if (in_plane(gm, off0, 2)) frame_ld2<T>(c, src.t + off0, F0, F1);
-    if (in_plane(gm, off0 - gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 - gm.pitch, s0, s1);  // j = 2: from y - 1
-    if (in_plane(gm, off0 + gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 + gm.pitch, n0, n1);  // j = 4: from y + 1
-    if (in_plane(gm, off0 - 1)) w = frame_ld<T>(c, src.t + off0 - 1);
-    if (in_plane(gm, off0 + 2)) e = frame_ld<T>(c, src.t + off0 + 2);
-    h0[1] += c.wt1 * (w - F0);
-    h1[1] += c.wt1 * (F0 - F1);
-    h0[2] += c.wt1 * (s0 - F0);
-    h1[2] += c.wt1 * (s1 - F1);
-    h0[3] += c.wt1 * (F1 - F0);
-    h1[3] += c.wt1 * (e - F1);
-    h0[4] += c.wt1 * (n0 - F0);
-    h1[4] += c.wt1 * (n1 - F1);
+    if constexpr (sizeof(typename FrameStore<T>::type) == 1) {
+        // 8-bit frames: differences taken on the integers, as in frame_in
+        char2 own = make_char2(0, 0), sth = own, nth = own;
+        signed char w = 0, e = 0;
+        if (in_plane(gm, off0, 2)) own = frame_pair_code<T>(src.t + off0);
+        if (in_plane(gm, off0 - gm.pitch, 2)) sth = frame_pair_code<T>(src.t + off0 - gm.pitch);  // j = 2: y - 1
+        if (in_plane(gm, off0 + gm.pitch, 2)) nth = frame_pair_code<T>(src.t + off0 + gm.pitch);  // j = 4: y + 1
+        if (in_plane(gm, off0 - 1)) w = (signed char)frame_code<T>(src.t + off0 - 1);
+        if (in_plane(gm, off0 + 2)) e = (signed char)frame_code<T>(src.t + off0 + 2);
+        const int k0 = (signed char)own.x, k1 = (signed char)own.y;
+        h0[1] += c.wt1fq * R((int)w - k0);
+        h1[1] += c.wt1fq * R(k0 - k1);
+        h0[2] += c.wt1fq * R((int)(signed char)sth.x - k0);
+        h1[2] += c.wt1fq * R((int)(signed char)sth.y - k1);
+        h0[3] += c.wt1fq * R(k1 - k0);
+        h1[3] += c.wt1fq * R((int)e - k1);
+        h0[4] += c.wt1fq * R((int)(signed char)nth.x - k0);
+        h1[4] += c.wt1fq * R((int)(signed char)nth.y - k1);
+        F0 = R(k0) * c.fq;
+        F1 = R(k1) * c.fq;
+    } else {
+        R n0 = R(0), n1 = R(0), s0 = R(0), s1 = R(0), w = R(0), e = R(0);
+        F0 = F1 = R(0);
+        if (in_plane(gm, off0, 2)) frame_ld2<T>(c, src.t + off0, F0, F1);
+        if (in_plane(gm, off0 - gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 - gm.pitch, s0, s1);  // j = 2: y - 1
+        if (in_plane(gm, off0 + gm.pitch, 2)) frame_ld2<T>(c, src.t + off0 + gm.pitch, n0, n1);  // j = 4: y + 1
+        if (in_plane(gm, off0 - 1)) w = frame_ld<T>(c, src.t + off0 - 1);
+        if (in_plane(gm, off0 + 2)) e = frame_ld<T>(c, src.t + off0 + 2);
+        h0[1] += c.wt1 * (w - F0);
+        h1[1] += c.wt1 * (F0 - F1);
+        h0[2] += c.wt1 * (s0 - F0);
+        h1[2] += c.wt1 * (s1 - F1);
+        h0[3] += c.wt1 * (F1 - F0);
+        h1[3] += c.wt1 * (e - F1);
+        h0[4] += c.wt1 * (n0 - F0);
+        h1[4] += c.wt1 * (n1 - F1);
+    }
 }
 
 // Framed storage: thermal values pulled into node off were stored in the
@@ -477,13 +515,25 @@ template <class T>
 __device__ __forceinline__ typename T::R frame_in(const Coef<typename T::R>& c, const Src<T>& src, const Geom& gm,
                                                   int off, typename T::R (&h)[5]) {
     using R = typename T::R;
-    const R F = in_plane(gm, off) ? frame_ld<T>(c, src.t + off) : R(0);
+    if constexpr (sizeof(typename FrameStore<T>::type) == 1) {
+        // 8-bit frames: w~_1 (F_s - F) = (w~_1 fq) (k_s - k), the same rounding, the
+        // difference taken on the integers
+        const int k = in_plane(gm, off) ? frame_code<T>(src.t + off) : 0;
 #pragma unroll
-    for (int j = 1; j < 5; ++j) {
-        const int o = off - ey9(j) * gm.pitch - ex9(j);
-        h[j] += c.wt1 * ((in_plane(gm, o) ? frame_ld<T>(c, src.t + o) : R(0)) - F);
+        for (int j = 1; j < 5; ++j) {
+            const int o = off - ey9(j) * gm.pitch - ex9(j);
+            h[j] += c.wt1fq * R((in_plane(gm, o) ? frame_code<T>(src.t + o) : 0) - k);
+        }
+        return R(k) * c.fq;
+    } else {
+        const R F = in_plane(gm, off) ? frame_ld<T>(c, src.t + off) : R(0);
+#pragma unroll
+        for (int j = 1; j < 5; ++j) {
+            const int o = off - ey9(j) * gm.pitch - ex9(j);
+            h[j] += c.wt1 * ((in_plane(gm, o) ? frame_ld<T>(c, src.t + o) : R(0)) - F);
+        }
+        return F;
     }
-    return F;
 }
 
 // T - T0 - F(x) at node off from the pulled thermal values (framed storage), and F(x).
