@@ -324,7 +324,11 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
  * 512 nodes run on 256-thread blocks, 32 or 64 nodes on one-warp blocks; the
  * larger size of each pair is two nodes per thread; tile_h = 0: runs of
  * tile_w consecutive nodes in each cavity's row-major order, wrapping onto
- * the next row, so no lanes idle at a cavity's right edge), blocks per SM (0 = as
+ * the next row, so no lanes idle at a cavity's right edge; tile_h = -1: runs
+ * of tile_w (32 to 256) pairs of nodes side by side along x, one pair per
+ * thread; tile_h = -2: the same over each cavity's interior pairs, with the
+ * wall nodes and their neighbours in tiles of their own, so that no warp of
+ * the interior branches into the wall rule), blocks per SM (0 = as
  * many as fit) and the scheduling without timing: dynamic = 0, each block
  * owns a contiguous run of tiles and a grid barrier ends every step; 1, blocks
  * take chunks of 4 tiles from a per-step counter, same barrier; 2, dataflow:

@@ -76,14 +76,55 @@ __host__ __device__ __forceinline__ Coef<R> with_cavity_rates(const Coef<R>& cu,
     return c;
 }
 
+// Split tiles (NPT = 4): a cavity's interior node pairs, (x0, x0 + 1) with
+// x0 = 2, 4, ..., 2 npi (npi = floor((nx - 3) / 2): the pairs clear of the
+// walls) and 1 <= y <= ny - 2, and its border, every other node: rows 0 and
+// ny - 1, then the columns 0, 1 and 2 npi + 2 .. nx - 1 of each inner row.
+// Border node b of a cavity, by that order.
+__device__ __forceinline__ void border_node(int b, int nx, int ny, int& x, int& y) {
+    if (b < 2 * nx) {
+        y = b < nx ? 0 : ny - 1;
+        x = b < nx ? b : b - nx;
+        return;
+    }
+    const int npi = (nx - 3) >> 1;
+    const int nbc = nx - 2 * npi;  // border columns per inner row: 0, 1 and the right edge
+    const int k = b - 2 * nx;
+    y = 1 + k / nbc;
+    const int col = k - (y - 1) * nbc;
+    x = col < 2 ? col : 2 * npi + col;
+}
+__host__ __device__ constexpr int border_count(int nx, int ny) { return 2 * nx + (ny - 2) * (nx - 2 * ((nx - 3) >> 1)); }
+
 // One tile of one step: tiles hold blockDim.x * NPT nodes (NPT = 3: two
 // nodes side by side along x per thread, a run of blockDim.x node pairs in
 // the row-major order of the cavity's pairs (x0 even), wrapping onto the next
-// rows; a row of odd width ends in a single node).
+// rows; a row of odd width ends in a single node.  NPT = 4: split tiles, a
+// run of blockDim.x interior pairs (y0 >= 1) or, y0 = -1, of blockDim.x
+// border nodes from index x0: the warps of interior tiles never branch into
+// the wall rule, which in a small cavity's pair runs would touch every warp).
 template <class T, int NPT>
 __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const Geom& gm, const Src<T>& src,
                                             const Dst<T>& dst, const Tile& tl, int lg_tw, int* status) {
-    if constexpr (NPT == 3) {
+    if constexpr (NPT == 4) {
+        if (tl.y0 < 0) {
+            const int b = tl.x0 + (int)threadIdx.x;
+            if (b < border_count(gm.nx, gm.ny)) {
+                int x, y;
+                border_node(b, gm.nx, gm.ny, x, y);
+                update_node<T, false>(c, gm, src, dst, nullptr, x, y, status);
+            }
+        } else {
+            const int npi = (gm.nx - 3) >> 1;
+            int xp = ((tl.x0 - 2) >> 1) + (int)threadIdx.x, y = tl.y0;
+            if (xp >= npi) {
+                const int q = xp / npi;
+                y += q;
+                xp -= q * npi;
+            }
+            if (y < gm.ny - 1) update_xpair<T, false>(c, gm, src, dst, nullptr, 2 + 2 * xp, y, status);
+        }
+    } else if constexpr (NPT == 3) {
         const int npx = (gm.nx + 1) >> 1;
         int xp = (tl.x0 >> 1) + (int)threadIdx.x, y = tl.y0;
         if (xp >= npx) {
@@ -112,7 +153,7 @@ __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const 
 // parameter cu, which instructions read from the constant bank; without
 // SPLIT all come from the descriptor (about 45 values per tile in registers).
 template <class T, int NPT, bool SPLIT>
-__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 1 ? 4 : 3) : 2)
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 2 ? 3 : 4) : 2)
     k_batch(const CavDesc<typename T::R>* __restrict__ cavs, const Tile* __restrict__ tiles, int ntiles, int lg_tw,
             int dyn, int* __restrict__ tile_ctr, long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
             long long wait_limit, int* __restrict__ status, int* __restrict__ timeout_flag,
@@ -320,12 +361,13 @@ struct TuneChoice {
     int tw = 128, th = 2, blocks_per_sm = 0, dyn = 0;
 };
 
-// th = -1: runs of tw node pairs (two nodes side by side along x per thread)
-int tile_nodes(const TuneChoice& t) { return t.th == -1 ? 2 * t.tw : (t.th == 0 ? t.tw : t.tw * t.th); }
+// th = -1: runs of tw node pairs (two nodes side by side along x per thread);
+// th = -2: split tiles, runs of tw interior pairs or tw border nodes
+int tile_nodes(const TuneChoice& t) { return t.th < 0 ? 2 * t.tw : (t.th == 0 ? t.tw : t.tw * t.th); }
 
 // Tiles of 256 or 512 nodes run with 256-thread blocks; tiles of 32 or 64
 // nodes with one-warp blocks, whose block synchronisation is a warp's.
-int block_of(const TuneChoice& t) { return t.th == -1 ? t.tw : (tile_nodes(t) >= 256 ? 256 : 32); }
+int block_of(const TuneChoice& t) { return t.th < 0 ? t.tw : (tile_nodes(t) >= 256 ? 256 : 32); }
 
 }  // namespace
 
@@ -380,8 +422,12 @@ int bfail(lbm_batch b, int code, const std::string& m) {
     } while (0)
 
 template <class T, bool SPLIT> const void* kernel_ptr(int npt) {
-    return npt == 3 ? (const void*)&k_batch<T, 3, SPLIT>
-                    : (npt == 2 ? (const void*)&k_batch<T, 2, SPLIT> : (const void*)&k_batch<T, 1, SPLIT>);
+    switch (npt) {
+        case 4: return (const void*)&k_batch<T, 4, SPLIT>;
+        case 3: return (const void*)&k_batch<T, 3, SPLIT>;
+        case 2: return (const void*)&k_batch<T, 2, SPLIT>;
+        default: return (const void*)&k_batch<T, 1, SPLIT>;
+    }
 }
 
 // FP64 keeps every coefficient in the descriptor: with the split its
@@ -393,7 +439,7 @@ const void* batch_kernel(int precision, int npt, bool split) {
     return split ? kernel_ptr<PrecF32QP, true>(npt) : kernel_ptr<PrecF32QP, false>(npt);
 }
 
-int npt_of(const TuneChoice& t) { return t.th == -1 ? 3 : (tile_nodes(t) == 2 * block_of(t) ? 2 : 1); }
+int npt_of(const TuneChoice& t) { return t.th == -2 ? 4 : t.th == -1 ? 3 : (tile_nodes(t) == 2 * block_of(t) ? 2 : 1); }
 
 int log2i(int v) {
     int l = 0;
@@ -409,7 +455,18 @@ int build_tiles(lbm_batch b) {
     b->cav_tiles.assign(b->ncav, 0);
     for (int c = 0; c < b->ncav; ++c) {
         const int nx = b->gm[c].nx, ny = b->gm[c].ny;
-        if (b->tune.th == -1) {
+        if (b->tune.th == -2) {
+            // interior pairs (x0 = 2 .. 2 npi, rows 1 .. ny - 2), then the border nodes
+            const long npi = (nx - 3) / 2;
+            for (long p0 = 0; p0 < npi * (ny - 2); p0 += b->tune.tw) {
+                tl.push_back(Tile{c, (int)(2 + 2 * (p0 % npi)), (int)(1 + p0 / npi)});
+                ++b->cav_tiles[c];
+            }
+            for (long b0 = 0; b0 < border_count(nx, ny); b0 += b->tune.tw) {
+                tl.push_back(Tile{c, (int)b0, -1});
+                ++b->cav_tiles[c];
+            }
+        } else if (b->tune.th == -1) {
             const long npx = (nx + 1) / 2;
             for (long p0 = 0; p0 < npx * ny; p0 += b->tune.tw) {
                 tl.push_back(Tile{c, (int)(2 * (p0 % npx)), (int)(p0 / npx)});
@@ -766,7 +823,7 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
     if (!cached) {
         const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 8}, {128, 4}, {256, 2}, {512, 1},
                                  {32, 1}, {32, 2}, {64, 1}, {32, 0}, {64, 0}, {256, 0}, {512, 0},
-                                 {32, -1}, {64, -1}, {128, -1}, {256, -1}};
+                                 {32, -1}, {64, -1}, {128, -1}, {256, -1}, {32, -2}, {64, -2}, {128, -2}, {256, -2}};
         const int occ[] = {0, 2};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -816,12 +873,13 @@ int lbm_batch_tune(lbm_batch b, const char* cache_path, int* tile_w, int* tile_h
 int lbm_batch_set_tiles(lbm_batch b, int tile_w, int tile_h, int blocks_per_sm, int dynamic) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     const int tn = tile_h == 0 ? tile_w : tile_w * tile_h;
-    const bool pairs = tile_h == -1 && (tile_w == 32 || tile_w == 64 || tile_w == 128 || tile_w == 256);
+    const bool pairs = (tile_h == -1 || tile_h == -2) && (tile_w == 32 || tile_w == 64 || tile_w == 128 || tile_w == 256);
     if (!pairs && (tile_w <= 0 || tile_h < 0 || (tn != 32 && tn != 64 && tn != 256 && tn != 512) ||
                    (tile_h > 0 && ((tile_w & (tile_w - 1)) != 0 || tile_w < 32)) || blocks_per_sm < 0))
         return bfail(b, LBM_ERR_ARG, "tiles hold 32, 64, 256 or 512 nodes: a power-of-two width >= 32 times "
                                      "tile_h rows, tile_h = 0 for runs of tile_w consecutive nodes, or "
-                                     "tile_h = -1 for runs of tile_w (32 to 256) node pairs");
+                                     "tile_h = -1 for runs of tile_w (32 to 256) node pairs, -2 for the same "
+                                     "over each cavity's interior with its border in runs of its own");
     if (blocks_per_sm < 0) return bfail(b, LBM_ERR_ARG, "blocks_per_sm < 0");
     b->tune.tw = tile_w;
     b->tune.th = tile_h;

@@ -52,10 +52,12 @@ def test_batch_matches_single_cavity_bit_for_bit():
     b.close()
 
 
-# (tile_w, tile_h, blocks_per_sm, scheduling); tile_h = 0: runs of tile_w consecutive nodes
+# (tile_w, tile_h, blocks_per_sm, scheduling); tile_h = 0: runs of tile_w consecutive nodes, -1: runs of
+# tile_w node pairs, -2: node pairs over each cavity's interior and its border in tiles of their own
 @pytest.mark.parametrize("tiles", [None, (64, 8, 0, 0), (32, 8, 0, 1), (128, 4, 2, 1), (32, 1, 0, 0),
                                    (32, 2, 0, 1), (64, 1, 0, 0), (32, 1, 0, 2), (32, 2, 0, 2), (128, 4, 0, 2),
-                                   (32, 0, 0, 0), (64, 0, 0, 1), (256, 0, 2, 0), (512, 0, 0, 2)])
+                                   (32, 0, 0, 0), (64, 0, 0, 1), (256, 0, 2, 0), (512, 0, 0, 2),
+                                   (64, -1, 0, 1), (32, -2, 0, 2), (128, -2, 0, 0)])
 def test_batch_fp64_matches_oracle(nthreads, tiles):
     from paper_1308_2071_gb300 import Batch
 
@@ -93,6 +95,34 @@ def test_one_node_tiles_are_bit_identical_to_the_single_cavity_kernel(tiles, pre
     for k, cv in enumerate(CAVS):
         c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision=precision,
                    nodes_per_thread=1)
+        c.step(300)
+        assert np.array_equal(np_(c.read_state()[0]), np_(b.read_state(k)[0])), k
+        assert np.array_equal(np_(c.read_state()[1]), np_(b.read_state(k)[1])), k
+        c.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tiles,precision", [((32, -1, 0, 1), "f32"), ((128, -1, 0, 2), "f32"),
+                                             ((32, -2, 0, 0), "f32"), ((64, -2, 0, 1), "f32"),
+                                             ((256, -2, 0, 2), "f32"), ((128, -2, 0, 1), "f32t")])
+def test_pair_tiles_are_bit_identical_to_the_single_cavity_pair_kernel(tiles, precision):
+    # runs of node pairs side by side along x (tile_h = -1), and the same over
+    # each cavity's interior with the border nodes in tiles of their own
+    # (tile_h = -2): every node runs the code of the single-cavity kernel in
+    # launch mode 3 (the pair code clear of the walls, the one-node code on
+    # and beside them), so the lattices are the same bit for bit, on even and
+    # odd widths and on a 5 x 7 cavity whose runs wrap over several rows
+    from paper_1308_2071_gb300 import Batch, Cavity
+
+    b = Batch(CAVS, precision=precision)
+    b.set_tiles(*tiles)
+    b.step(137)
+    b.step(163)
+    rc, st = b.status()
+    assert rc == 0
+    for k, cv in enumerate(CAVS):
+        c = Cavity(cv["nx"], cv["ny"], Ra=cv["Ra"], Da=cv["Da"], phi=cv["phi"], precision=precision,
+                   nodes_per_thread=3, block_x=32, block_y=4)
         c.step(300)
         assert np.array_equal(np_(c.read_state()[0]), np_(b.read_state(k)[0])), k
         assert np.array_equal(np_(c.read_state()[1]), np_(b.read_state(k)[1])), k
