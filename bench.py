@@ -415,9 +415,10 @@ def batched_leg(steps, warmup, ncav=256, seed=2071):
     gbs = nodes * BYTES_PER_NODE["f32"] / (ms * 1e-3 / steps) / 1e9  # 114 B per node-step
     return dict(cavities=ncav, nodes=nodes, steps=steps, mlups=round(nodes * steps / (ms * 1e-3) / 1e6, 2),
                 hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / peak, 4), tile=[tw, th], blocks_per_sm=bps,
-                tile_kind=("runs of node pairs side by side along x" if th == -1 else
+                tile_kind=("interior node pairs side by side along x, border nodes in tiles of their own"
+                           if th == -2 else "runs of node pairs side by side along x" if th == -1 else
                            "runs of consecutive nodes" if th == 0 else "rectangles"),
-                nodes_per_thread=(2 if th == -1 else 1 if (tw if th == 0 else tw * th) in (32, 256) else 2),
+                nodes_per_thread=(2 if th < 0 else 1 if (tw if th == 0 else tw * th) in (32, 256) else 2),
                 mode="one persistent cooperative launch per call, graph-captured",
                 blocks=q["nblocks"], tiles=q["ntiles"], launches=1, diverged=int(st.sum()),
                 status=int(rc), sizes="U{64..512} square, seed %d" % seed)

@@ -79,8 +79,9 @@ __host__ __device__ __forceinline__ Coef<R> with_cavity_rates(const Coef<R>& cu,
 // Split tiles (NPT = 4): a cavity's interior node pairs, (x0, x0 + 1) with
 // x0 = 2, 4, ..., 2 npi (npi = floor((nx - 3) / 2): the pairs clear of the
 // walls) and 1 <= y <= ny - 2, and its border, every other node: rows 0 and
-// ny - 1, then the columns 0, 1 and 2 npi + 2 .. nx - 1 of each inner row.
-// Border node b of a cavity, by that order.
+// ny - 1, then the columns 0, 1 and 2 npi + 2 .. nx - 1 of each inner row
+// (the nodes of the pairs that touch a wall).  Border node b of a cavity, by
+// that order.
 __device__ __forceinline__ void border_node(int b, int nx, int ny, int& x, int& y) {
     if (b < 2 * nx) {
         y = b < nx ? 0 : ny - 1;
@@ -115,14 +116,19 @@ __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const 
                 update_node<T, false>(c, gm, src, dst, nullptr, x, y, status);
             }
         } else {
-            const int npi = (gm.nx - 3) >> 1;
-            int xp = ((tl.x0 - 2) >> 1) + (int)threadIdx.x, y = tl.y0;
-            if (xp >= npi) {
-                const int q = xp / npi;
+            // the pairs of the inner rows in row-major order, as in pair runs (so a
+            // warp's accesses start on the rows' 128-byte boundaries); the lanes
+            // whose pair touches a wall idle, the border tiles take those nodes
+            const int npx = (gm.nx + 1) >> 1;
+            int xp = (tl.x0 >> 1) + (int)threadIdx.x, y = tl.y0;
+            if (xp >= npx) {
+                const int q = xp / npx;
                 y += q;
-                xp -= q * npi;
+                xp -= q * npx;
             }
-            if (y < gm.ny - 1) update_xpair<T, false>(c, gm, src, dst, nullptr, 2 + 2 * xp, y, status);
+            const int x0 = 2 * xp;
+            if (y < gm.ny - 1 && x0 > 0 && x0 + 1 < gm.nx - 1)
+                update_xpair<T, false>(c, gm, src, dst, nullptr, x0, y, status);
         }
     } else if constexpr (NPT == 3) {
         const int npx = (gm.nx + 1) >> 1;
@@ -456,10 +462,10 @@ int build_tiles(lbm_batch b) {
     for (int c = 0; c < b->ncav; ++c) {
         const int nx = b->gm[c].nx, ny = b->gm[c].ny;
         if (b->tune.th == -2) {
-            // interior pairs (x0 = 2 .. 2 npi, rows 1 .. ny - 2), then the border nodes
-            const long npi = (nx - 3) / 2;
-            for (long p0 = 0; p0 < npi * (ny - 2); p0 += b->tune.tw) {
-                tl.push_back(Tile{c, (int)(2 + 2 * (p0 % npi)), (int)(1 + p0 / npi)});
+            // the pairs of the inner rows (those clear of the walls run there), then the border nodes
+            const long npx = (nx + 1) / 2;
+            for (long p0 = 0; p0 < npx * (ny - 2); p0 += b->tune.tw) {
+                tl.push_back(Tile{c, (int)(2 * (p0 % npx)), (int)(1 + p0 / npx)});
                 ++b->cav_tiles[c];
             }
             for (long b0 = 0; b0 < border_count(nx, ny); b0 += b->tune.tw) {
