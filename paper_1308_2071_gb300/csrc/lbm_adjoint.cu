@@ -252,10 +252,11 @@ cudaError_t adjoint_sweep(const AdjointJob& J) {
     if (e0 == cudaSuccess) e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<T>, 256, 0);
     if (e0 != cudaSuccess) return e0;
     const long inner = (long)(gm.nx - 4) * (gm.ny - 4), ring = 4L * gm.nx + 4L * (gm.ny - 4);
-    // one interior block per SM less than fits, so that a 64-thread ring block
-    // finds registers beside the interior blocks and both kernels run at once
-    const long want = (long)nsm * (per_sm > 1 ? per_sm - 1 : 1);
-    const int nblk = (int)std::max(1L, std::min(want, (inner + 255) / 256));
+    // one interior node per thread: the hardware starts the blocks of the
+    // next wave as blocks finish (a grid-stride loop over fewer resident
+    // blocks ran its last pass with a fifth of the threads busy)
+    (void)per_sm;
+    const int nblk = (int)std::max(1L, (inner + 255) / 256);
     const int nring = (int)std::max(1L, std::min((long)nsm, (ring + 63) / 64));
     const int nseg = (N + K - 1) / K;
     R* M[2] = {(R*)J.madj, (R*)J.madj + (size_t)gm.plane * NPOP};
