@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--field", action="store_true",
                     help="the heterogeneous workload (log-normal porosity field) at --size, for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--long-size", type=int, default=1024,
+                    help="lattice of the long_run leg (config 2's 50,000 steps against FP64)")
     ap.add_argument("--leg", default=None, choices=["batched", "adjoint", "heterogeneous", "e2e", "long_run"],
                     help="run only this extra leg and print its result (profiling)")
     return ap.parse_args()
@@ -580,7 +582,8 @@ def main():
     _lib.load()
     if a.leg:
         legs = dict(batched=lambda: batched_leg(min(a.steps, 1000), min(a.warmup, 8)),
-                    adjoint=adjoint_leg, heterogeneous=heterogeneous_leg, long_run=long_run_leg,
+                    adjoint=adjoint_leg, heterogeneous=heterogeneous_leg,
+                    long_run=lambda: long_run_leg(a.long_size),
                     e2e=lambda: e2e_leg(a.size, a.precision, min(a.steps, 1000)))
         print(json.dumps({"leg": a.leg, a.leg: legs[a.leg]()}), flush=True)
         return

@@ -243,7 +243,10 @@ int lbm_read_state(lbm_handle h, double* f_dev, double* g_dev);
  * observable at t_n comes from it, and lbm_load() rebuilds B_n from it with
  * one step, so a handle that loads it continues exactly as the handle that
  * saved it would, given the same launch shape (lbm_tune).  Version-1
- * checkpoints (B_{n-1} then B_n) are still read.  lbm_checkpoint_size() gives
+ * checkpoints (B_{n-1} then B_n) and version 2 are still read for LBM_F64 and
+ * LBM_F32_FRAMED, whose layout they share; LBM_F32 and LBM_F32_STORE_F16
+ * lattices of those versions (stored without temperature frames) are
+ * refused with LBM_ERR_ARG.  lbm_checkpoint_size() gives
  * the byte count; lbm_save() writes it into a caller-owned host buffer of at
  * least that size (synchronises the stream); lbm_load() restores it into a
  * handle created with the same nx, ny and precision (synchronises the
@@ -274,9 +277,14 @@ int lbm_load(lbm_handle h, const void* host, size_t bytes);
  * make that first call before any stream capture.  All calls share the array
  * and it keeps the previous call's contents (the status word is cleared on
  * entry), so calls that overlap on the GPU race: serialise them.
+ * A checkpoint carries no divergence flag of the steps that made it, so the
+ * state itself is tested: a non-finite value anywhere (the maximum of |u|
+ * keeps NaN) or |u| >= 1/2 sets out->status and returns LBM_ERR_DIVERGED,
+ * with *out and the fields filled.
  * Errors: LBM_ERR_ARG (invalid parameters, use_phi_field set, a lattice
  * beyond 32-bit offsets, a buffer smaller than the lattice needs, a header
- * that does not match p), LBM_ERR_CUDA; lbm_last_error(NULL) describes it. */
+ * that does not match p, a checkpoint of an older storage layout),
+ * LBM_ERR_DIVERGED, LBM_ERR_CUDA; lbm_last_error(NULL) describes it. */
 int lbm_observables_noalloc(const lbm_params* p, const void* ckpt_dev, size_t bytes, void* stream,
                             lbm_obs* out, void* ux_dev, void* uy_dev, void* T_dev, void* p_dev);
 
