@@ -329,6 +329,8 @@ __host__ __device__ inline void wall_node_forward(const Coef<R>& c, const Tape<R
         const R cP = (i == 0) ? R(-5.0 / 3.0) : R(3.0 * w9(i));
         d[i] = df[i] - si + cP * ddP;
     }
+    mb.dux = -mom_x(d);
+    mb.duy = -mom_y(d);
     const R ddT = mb.dT - tf.dT;
     const R adv = (c.T0 + tf.dT) * c.inv_sigma * c.inv_csT2 * c.wt1;
     h[0] = hf[0] + c.wt0 * ddT;
@@ -352,6 +354,8 @@ __host__ __device__ inline void fluid_node_forward(const Coef<R>& c, R phi, R (&
     m.dT = t.dT;
     m.Fx = t.Fx;
     m.Fy = t.Fy;
+    m.dux = t.ux - mom_x(d);
+    m.duy = t.uy - mom_y(d);
     collide<R>(c, t.iphi, m, d, h);
 }
 

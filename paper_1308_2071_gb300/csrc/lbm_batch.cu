@@ -159,7 +159,7 @@ __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const 
 // parameter cu, which instructions read from the constant bank; without
 // SPLIT all come from the descriptor (about 45 values per tile in registers).
 template <class T, int NPT, bool SPLIT>
-__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? (NPT == 2 ? 3 : 4) : 2)
+__global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 3 : 2)
     k_batch(const CavDesc<typename T::R>* __restrict__ cavs, const Tile* __restrict__ tiles, int ntiles, int lg_tw,
             int dyn, int* __restrict__ tile_ctr, long nsteps, int par, unsigned* bar_count, unsigned* bar_gen,
             long long wait_limit, int* __restrict__ status, int* __restrict__ timeout_flag,

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // ---- lattice -----------------------------------------------------------------
@@ -139,6 +141,10 @@ struct PrecF16 {
     static constexpr bool framed = true;
     using ST = int8_t;
 };
+// Increment-form collision (see collide) for the FP32 storage variants.
+template <class T> struct IncForm {
+    static constexpr bool value = std::is_same<typename T::R, float>::value && std::is_same<typename T::SF, float>::value;
+};
 template <class T, class = void> struct Paired {
     static constexpr bool value = false;
 };
@@ -238,8 +244,38 @@ __device__ __forceinline__ F2 operator-(F2 a, float b) { return a - F2(b); }
 __device__ __forceinline__ F2 operator*(float a, F2 b) { return F2(a) * b; }
 __device__ __forceinline__ F2 operator*(F2 a, float b) { return a * F2(b); }
 __device__ __forceinline__ F2 sqrt(F2 a) { return F2(sqrtf(a.v.x), sqrtf(a.v.y)); }
+__device__ __forceinline__ F2 div_small(F2 a, F2 b) { return F2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)); }
 }  // namespace x2
 using x2::F2;
+
+// a / b for quotients that only scale a small correction (b near 1): the
+// fast FP32 division (2 ulp) there, IEEE division in FP64.
+__host__ __device__ __forceinline__ double div_small(double a, double b) { return a / b; }
+__host__ __device__ __forceinline__ float div_small(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
+// Sum of the thermal values h (T - T0, or T - T0 - F framed, without the
+// source half-step): in the association of n_0 in the increment-form
+// collision when INC, else left to right.  Every place that forms a
+// temperature from pulled values uses this, so they agree bit for bit.
+template <bool INC, class R> __host__ __device__ __forceinline__ R heat_sum(const R (&h)[5]) {
+    if constexpr (INC) return ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+    return h[0] + h[1] + h[2] + h[3] + h[4];
+}
+
+// x and y momentum of deviations d (m_3 and m_5 of Eq. 9-11), with one
+// association of the sums wherever they are taken.
+template <class R> __host__ __device__ __forceinline__ R mom_x(const R (&d)[9]) {
+    return (d[1] - d[3]) + ((d[5] - d[6]) - (d[7] - d[8]));
+}
+template <class R> __host__ __device__ __forceinline__ R mom_y(const R (&d)[9]) {
+    return (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));
+}
 
 // ---- per-launch coefficients ----------------------------------------------------
 
@@ -548,13 +584,14 @@ __device__ __forceinline__ typename T::R pull_heat_framed(const Coef<typename T:
         h[j] = in_plane(gm, o) ? Conv<typename T::SG, R, T::cg>::ld(src.g + j * gm.plane + o) : R(0);
     }
     F = frame_in<T>(c, src, gm, off, h);
-    return h[0] + h[1] + h[2] + h[3] + h[4];
+    return heat_sum<IncForm<T>::value>(h);
 }
 
 // ---- macroscopic values -------------------------------------------------------------
 
 template <class R> struct Macro {
     R ux, uy;  // velocity (Eq. 21)
+    R dux, duy;  // u - j, j = (m_3, m_5) of the populations the collision starts from
     R dP;      // phi p - rho0 c_s^2 (Eq. 23)
     R dT;      // T - T0 (Eq. 36)
     R Fx, Fy;  // total force (Eq. 4)
@@ -565,30 +602,56 @@ template <class R> struct Macro {
 // Eq. 36, Section 2 buoyancy, Eq. 22, Eq. 21, Eq. 23, Eq. 4 at a fluid node.
 // CR: type of the coefficients (R, or float for the node pair F2).  FR: the
 // thermal values h are relative to the frame F (framed storage).
-template <class R, class CR, bool FR = false>
+template <class R, class CR, bool FR = false, bool INC = false>
 __device__ __forceinline__ Macro<R> fluid_macros(const Coef<CR>& c, const Drag<R>& dr,
                                                  const R (&d)[9], const R (&h)[5], R F = R(0)) {
     Macro<R> m;
+    // n_0 of the thermal collision (INC: summed in its association)
+    const R n0 = heat_sum<INC>(h);
     if constexpr (FR) {
         m.F = F;
-        m.dTl = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+        m.dTl = n0 + c.qhalf;
         m.dT = F + m.dTl;
     } else {
-        m.dT = (h[0] + h[1] + h[2] + h[3] + h[4]) + c.qhalf;
+        m.dT = n0 + c.qhalf;
         m.dTl = m.dT;
     }
     const R Gy = c.gbeta * m.dT;
-    const R jx = (d[1] - d[3]) + (d[5] - d[6]) - (d[7] - d[8]);
-    const R jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R jx = INC ? mom_x(d) : (d[1] - d[3]) + (d[5] - d[6]) - (d[7] - d[8]);
+    const R jy = INC ? mom_y(d) : (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const R by = R(0.5) * dr.phi * Gy;  // half the buoyancy impulse
     const R vx = jx;
-    const R vy = jy + R(0.5) * dr.phi * Gy;
-    const R l0 = R(0.5) + R(0.25) * dr.c_lin;
+    const R vy = jy + by;
+    // Eq. 22, u = v / (l0 + sqrt(l0^2 + l1 |v|)) with l0 = 1/2 + c_lin/4, written
+    // as u = v - v g / (1 + g), g = l0 + sqrt(l0^2 + l1 |v|) - 1 (of the order
+    // of the drag per step): the collision adds u - j to the momentum, and
+    // that difference is formed here from small terms only, so its rounding
+    // scales with g and not with |u|.  (Formed as u - j from a rounded u, the
+    // error would be a fixed fraction of u per step, which the slow Darcy
+    // relaxation integrates into a velocity error of order 1e-7 / drag.)
+    // The direct form without INC (FP64 and FP16-flow storage, see collide).
     const R l1 = R(0.5) * dr.c_quad;
     const R vm = sqrt(vx * vx + vy * vy);
-    const R den = R(1) / (l0 + sqrt(l0 * l0 + l1 * vm));
-    m.ux = vx * den;
-    m.uy = vy * den;
-    m.umag = vm * den;
+    if constexpr (INC) {
+        const R cc = R(0.25) * dr.c_lin;
+        const R e = cc + cc * cc + l1 * vm;  // l0^2 + l1 |v| - 1/4
+        const R g = cc + div_small(e, sqrt(R(0.25) + e) + R(0.5));
+        const R den = div_small(R(1), R(1) + g);
+        const R gd = g * den;
+        m.dux = -(vx * gd);
+        m.duy = by - vy * gd;
+        m.ux = jx + m.dux;
+        m.uy = jy + m.duy;
+        m.umag = vm * den;
+    } else {
+        const R l0 = R(0.5) + R(0.25) * dr.c_lin;
+        const R den = R(1) / (l0 + sqrt(l0 * l0 + l1 * vm));
+        m.ux = vx * den;
+        m.uy = vy * den;
+        m.umag = vm * den;
+        m.dux = m.ux - jx;
+        m.duy = m.uy - jy;
+    }
     const R uu = m.ux * m.ux + m.uy * m.uy;
     const R s18 = (d[1] + d[2] + d[3] + d[4]) + (d[5] + d[6] + d[7] + d[8]);
     // c_s^2 / (1 - w_0) = 3/5 and rho0 s_0(u) = -(2/3) |u|^2 / phi
@@ -604,11 +667,20 @@ __device__ __forceinline__ Macro<R> fluid_macros(const Coef<CR>& c, const Drag<R
 // Eq. 17 with m_eq of Eq. 16 and S of Eq. 19, then f+ = M^-1 m+ (Eq. 18,
 // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4));
 // Eq. 34 with n_eq of Eq. 29 and Psi of Eq. 30, then g+ = N^-1 n+ (Eq. 35,
-// N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h.
-template <class R, class CR, bool FR = false>
+// N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)).  In place on d and h, as
+// increments: f+ = f + M^-1 (m+ - m), g+ = g + N^-1 (n+ - n).  Equal in exact
+// arithmetic; in FP32 the rounded factors 1/9, 1/6, 1/36, 1/5 ... then scale
+// the change of a step instead of the whole moment, where 6 fl(1/6) != 1
+// would bias the momentum by 3e-8 of itself every step (a velocity error
+// of 3e-8 / drag once the Darcy relaxation has integrated it).  INC = false
+// forms f+ = M^-1 m+ from the new moments instead (the same in exact
+// arithmetic; fewer live registers): FP64, whose rounding is far below
+// that bias, and FP16-flow storage, whose rounding is far above it.
+template <class R, class CR, bool FR = false, bool INC = false>
 __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, const Macro<R>& mc, R (&d)[9],
                                         R (&h)[5]) {
-    // m = M d (Eq. 9-11), as a deviation from the rest moments
+    // m = M d (Eq. 9-11), as a deviation from the rest moments; m_3 - u_x
+    // and m_5 - u_y come with the macroscopic values (mc.dux, mc.duy)
     const R a = (d[1] + d[2]) + (d[3] + d[4]);
     const R b = (d[5] + d[6]) + (d[7] + d[8]);
     const R ex13 = d[1] - d[3], ey24 = d[2] - d[4];
@@ -617,9 +689,7 @@ __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, cons
     const R m0 = d[0] + a + b;
     const R m1 = R(-4) * d[0] - a + R(2) * b;
     const R m2 = R(4) * d[0] - R(2) * a + b;
-    const R m3 = ex13 + dx;
     const R m4 = R(-2) * ex13 + dx;
-    const R m5 = ey24 + dy;
     const R m6 = R(-2) * ey24 + dy;
     const R m7 = (d[1] - d[2]) + (d[3] - d[4]);
     const R m8 = (d[5] - d[6]) + (d[7] - d[8]);
@@ -638,34 +708,61 @@ __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, cons
     const R S7 = R(2) * (ux * mc.Fx - uy * mc.Fy) * iphi;
     const R S8 = (ux * mc.Fy + uy * mc.Fx) * iphi;
 
-    // Eq. 17: m+ = m - s (m - m_eq) + (1 - s/2) S, scaled by the diagonal of M^-1
-    const R p0 = (m0 - c.s[0] * m0) * R(1.0 / 9.0);
-    const R p1 = (m1 - c.s[1] * (m1 - eq1) + c.hs[1] * S1) * R(1.0 / 36.0);
-    const R p2 = (m2 - c.s[2] * (m2 - eq2) - c.hs[2] * S1) * R(1.0 / 36.0);
-    const R p3 = (m3 - c.s[3] * (m3 - ux) + c.hs[3] * mc.Fx) * R(1.0 / 6.0);
-    const R p4 = (m4 - c.s[4] * (m4 + ux) - c.hs[4] * mc.Fx) * R(1.0 / 12.0);
-    const R p5 = (m5 - c.s[5] * (m5 - uy) + c.hs[5] * mc.Fy) * R(1.0 / 6.0);
-    const R p6 = (m6 - c.s[6] * (m6 + uy) - c.hs[6] * mc.Fy) * R(1.0 / 12.0);
-    const R p7 = (m7 - c.s[7] * (m7 - eq7) + c.hs[7] * S7) * R(0.25);
-    const R p8 = (m8 - c.s[8] * (m8 - eq8) + c.hs[8] * S8) * R(0.25);
+    // Eq. 17: m+ - m = -s (m - m_eq) + (1 - s/2) S (INC: that alone, else
+    // with m added), scaled by the diagonal of M^-1
+    R p0, p1, p2, p3, p4, p5, p6, p7, p8;
+    if constexpr (INC) {
+        p0 = -(c.s[0] * m0) * R(1.0 / 9.0);
+        p1 = (c.hs[1] * S1 - c.s[1] * (m1 - eq1)) * R(1.0 / 36.0);
+        p2 = (-(c.hs[2] * S1) - c.s[2] * (m2 - eq2)) * R(1.0 / 36.0);
+        p3 = (c.s[3] * mc.dux + c.hs[3] * mc.Fx) * R(1.0 / 6.0);
+        p4 = (-(c.hs[4] * mc.Fx) - c.s[4] * (m4 + ux)) * R(1.0 / 12.0);
+        p5 = (c.s[5] * mc.duy + c.hs[5] * mc.Fy) * R(1.0 / 6.0);
+        p6 = (-(c.hs[6] * mc.Fy) - c.s[6] * (m6 + uy)) * R(1.0 / 12.0);
+        p7 = (c.hs[7] * S7 - c.s[7] * (m7 - eq7)) * R(0.25);
+        p8 = (c.hs[8] * S8 - c.s[8] * (m8 - eq8)) * R(0.25);
+    } else {
+        const R m3 = ex13 + dx, m5 = ey24 + dy;
+        p0 = (m0 - c.s[0] * m0) * R(1.0 / 9.0);
+        p1 = (m1 - c.s[1] * (m1 - eq1) + c.hs[1] * S1) * R(1.0 / 36.0);
+        p2 = (m2 - c.s[2] * (m2 - eq2) - c.hs[2] * S1) * R(1.0 / 36.0);
+        p3 = (m3 - c.s[3] * (m3 - ux) + c.hs[3] * mc.Fx) * R(1.0 / 6.0);
+        p4 = (m4 - c.s[4] * (m4 + ux) - c.hs[4] * mc.Fx) * R(1.0 / 12.0);
+        p5 = (m5 - c.s[5] * (m5 - uy) + c.hs[5] * mc.Fy) * R(1.0 / 6.0);
+        p6 = (m6 - c.s[6] * (m6 + uy) - c.hs[6] * mc.Fy) * R(1.0 / 12.0);
+        p7 = (m7 - c.s[7] * (m7 - eq7) + c.hs[7] * S7) * R(0.25);
+        p8 = (m8 - c.s[8] * (m8 - eq8) + c.hs[8] * S8) * R(0.25);
+    }
 
     // f+ = M^T p (columns of Eq. 11)
     const R r1 = p0 - p1 - R(2) * p2;  // common part of the axis directions
     const R r5 = p0 + R(2) * p1 + p2;  // common part of the diagonals
     const R x34 = p3 - R(2) * p4, y56 = p5 - R(2) * p6;
     const R x34d = p3 + p4, y56d = p5 + p6;
-    d[0] = p0 - R(4) * p1 + R(4) * p2;
-    d[1] = r1 + x34 + p7;
-    d[2] = r1 + y56 - p7;
-    d[3] = r1 - x34 + p7;
-    d[4] = r1 - y56 - p7;
-    d[5] = r5 + x34d + y56d + p8;
-    d[6] = r5 - x34d + y56d - p8;
-    d[7] = r5 - x34d - y56d + p8;
-    d[8] = r5 + x34d - y56d - p8;
+    if constexpr (INC) {
+        d[0] = d[0] + (p0 - R(4) * p1 + R(4) * p2);
+        d[1] = d[1] + (r1 + x34 + p7);
+        d[2] = d[2] + (r1 + y56 - p7);
+        d[3] = d[3] + (r1 - x34 + p7);
+        d[4] = d[4] + (r1 - y56 - p7);
+        d[5] = d[5] + (r5 + x34d + y56d + p8);
+        d[6] = d[6] + (r5 - x34d + y56d - p8);
+        d[7] = d[7] + (r5 - x34d - y56d + p8);
+        d[8] = d[8] + (r5 + x34d - y56d - p8);
+    } else {
+        d[0] = p0 - R(4) * p1 + R(4) * p2;
+        d[1] = r1 + x34 + p7;
+        d[2] = r1 + y56 - p7;
+        d[3] = r1 - x34 + p7;
+        d[4] = r1 - y56 - p7;
+        d[5] = r5 + x34d + y56d + p8;
+        d[6] = r5 - x34d + y56d - p8;
+        d[7] = r5 - x34d - y56d + p8;
+        d[8] = r5 + x34d - y56d - p8;
+    }
 
     // thermal: n = N h (Eq. 27-28), deviation from T0 (1, 0, 0, varpi, 0)
-    const R n0 = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
+    const R n0 = INC ? ((h[0] + h[1]) + (h[2] + h[3])) + h[4] : (h[0] + h[1]) + (h[2] + h[3]) + h[4];
     const R n1 = h[1] - h[3];
     const R n2 = h[2] - h[4];
     const R n3 = R(-4) * h[0] + (h[1] + h[2]) + (h[3] + h[4]);
@@ -677,16 +774,30 @@ __host__ __device__ __forceinline__ void collide(const Coef<CR>& c, R iphi, cons
     // T0 + F, the flux part (u T / sigma) uses the absolute T
     const R dTn = FR ? mc.dTl : mc.dT;
     const R ne3 = c.varpi * dTn;
-    const R q0 = (n0 - c.z[0] * (n0 - dTn) + c.hz[0] * c.psi0) * R(0.2);
-    const R q1 = (n1 - c.z[1] * (n1 - ne1)) * R(0.5);
-    const R q2 = (n2 - c.z[2] * (n2 - ne2)) * R(0.5);
-    const R q3 = (n3 - c.z[3] * (n3 - ne3) + c.hz[3] * c.psi3) * R(0.05);
-    const R q4 = (n4 - c.z[4] * n4) * R(0.25);
-    h[0] = q0 - R(4) * q3;
-    h[1] = q0 + q1 + q3 + q4;
-    h[2] = q0 + q2 + q3 - q4;
-    h[3] = q0 - q1 + q3 + q4;
-    h[4] = q0 - q2 + q3 - q4;
+    if constexpr (INC) {
+        // Eq. 34 as n+ - n = -zeta (n - n_eq) + (1 - zeta/2) Psi
+        const R q0 = (c.hz[0] * c.psi0 - c.z[0] * (n0 - dTn)) * R(0.2);
+        const R q1 = -(c.z[1] * (n1 - ne1)) * R(0.5);
+        const R q2 = -(c.z[2] * (n2 - ne2)) * R(0.5);
+        const R q3 = (c.hz[3] * c.psi3 - c.z[3] * (n3 - ne3)) * R(0.05);
+        const R q4 = -(c.z[4] * n4) * R(0.25);
+        h[0] = h[0] + (q0 - R(4) * q3);
+        h[1] = h[1] + (q0 + q1 + q3 + q4);
+        h[2] = h[2] + (q0 + q2 + q3 - q4);
+        h[3] = h[3] + (q0 - q1 + q3 + q4);
+        h[4] = h[4] + (q0 - q2 + q3 - q4);
+    } else {
+        const R q0 = (n0 - c.z[0] * (n0 - dTn) + c.hz[0] * c.psi0) * R(0.2);
+        const R q1 = (n1 - c.z[1] * (n1 - ne1)) * R(0.5);
+        const R q2 = (n2 - c.z[2] * (n2 - ne2)) * R(0.5);
+        const R q3 = (n3 - c.z[3] * (n3 - ne3) + c.hz[3] * c.psi3) * R(0.05);
+        const R q4 = (n4 - c.z[4] * n4) * R(0.25);
+        h[0] = q0 - R(4) * q3;
+        h[1] = q0 + q1 + q3 + q4;
+        h[2] = q0 + q2 + q3 - q4;
+        h[3] = q0 - q1 + q3 + q4;
+        h[4] = q0 - q2 + q3 - q4;
+    }
 }
 
 // ---- wall rule ----------------------------------------------------------------------------
@@ -724,7 +835,7 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
         Fb = in_plane(gm, y * gm.pitch + x) ? frame_ld<T>(c, src.t + y * gm.pitch + x) : R(0);
     }
     const Drag<R> drf = drag_at<R, FIELD, typename T::P>(c, gm, phi_field, offf);
-    const Macro<R> mf = fluid_macros<R, R, FR>(c, drf, df, hf, Ff);
+    const Macro<R> mf = fluid_macros<R, R, FR, IncForm<T>::value>(c, drf, df, hf, Ff);
 
     Macro<R> mb;
     mb.ux = R(0);
@@ -778,6 +889,8 @@ __device__ __forceinline__ Macro<typename T::R> wall_node(const Coef<typename T:
         const R cP = (i == 0) ? R(-5.0 / 3.0) : R(3.0 * w9(i));
         d[i] = df[i] - si + cP * ddP;
     }
+    mb.dux = -mom_x(d);  // u_b = 0
+    mb.duy = -mom_y(d);
     // g_b = g_eq(T_b, 0) + g_f - g_eq(T_f, u_f) (Eq. 37, first occurrence); framed:
     // T_b - T_f from the frames' difference and the local parts, the result
     // re-expressed in this node's frame
@@ -809,9 +922,9 @@ __device__ __forceinline__ Macro<typename T::R> node_state(const Coef<typename T
         pull<T>(src, gm, off, d, h);
         if constexpr (Framed<T>::value) {
             const R F = frame_in<T>(c, src, gm, off, h);
-            return fluid_macros<R, R, true>(c, dr, d, h, F);
+            return fluid_macros<R, R, true, IncForm<T>::value>(c, dr, d, h, F);
         }
-        return fluid_macros<R>(c, dr, d, h);
+        return fluid_macros<R, R, false, IncForm<T>::value>(c, dr, d, h);
     }
     return wall_node<T, FIELD>(c, gm, src, phi_field, x, y, nr, dr, d, h);
 }
@@ -869,7 +982,7 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     Drag<R> dr;
     const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
     if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
-    collide<R, R, Framed<T>::value>(c, dr.iphi, mc, d, h);
+    collide<R, R, Framed<T>::value, IncForm<T>::value>(c, dr.iphi, mc, d, h);
     const int off = y * gm.pitch + x;
     if constexpr (Framed<T>::value) frame_out<T>(c, gm, dst, off, mc, h);
     if (in_plane(gm, off)) {
@@ -1007,11 +1120,11 @@ __device__ __forceinline__ void update_pair(const Coef<typename T::R>& c, const 
         }
         const Drag<R> dr0 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off0);
         const Drag<R> dr1 = drag_at<R, FIELD, typename T::P>(c, gm, phi, off1);
-        const Macro<R> m0 = fluid_macros<R, R, FR>(c, dr0, d0, h0, F0);
-        const Macro<R> m1 = fluid_macros<R, R, FR>(c, dr1, d1, h1, F1);
+        const Macro<R> m0 = fluid_macros<R, R, FR, IncForm<T>::value>(c, dr0, d0, h0, F0);
+        const Macro<R> m1 = fluid_macros<R, R, FR, IncForm<T>::value>(c, dr1, d1, h1, F1);
         if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
-        collide<R, R, FR>(c, dr0.iphi, m0, d0, h0);
-        collide<R, R, FR>(c, dr1.iphi, m1, d1, h1);
+        collide<R, R, FR, IncForm<T>::value>(c, dr0.iphi, m0, d0, h0);
+        collide<R, R, FR, IncForm<T>::value>(c, dr1.iphi, m1, d1, h1);
         if constexpr (FR) {
             frame_out<T>(c, gm, dst, off0, m0, h0);
             frame_out<T>(c, gm, dst, off1, m1, h1);
@@ -1061,11 +1174,11 @@ __device__ __forceinline__ void update_xpair(const Coef<typename T::R>& c, const
             collide_fluid_pair_x2<T, OBS, true>(c, gm, dst, d0, h0, d1, h1, dr0, dr1, off0, off1, status, x0, y, x1,
                                                 y, obs, F0, F1);
         } else {
-            const Macro<R> m0 = fluid_macros<R, R, FR>(c, dr0, d0, h0, F0);
-            const Macro<R> m1 = fluid_macros<R, R, FR>(c, dr1, d1, h1, F1);
+            const Macro<R> m0 = fluid_macros<R, R, FR, IncForm<T>::value>(c, dr0, d0, h0, F0);
+            const Macro<R> m1 = fluid_macros<R, R, FR, IncForm<T>::value>(c, dr1, d1, h1, F1);
             if (!(m0.umag < R(0.5)) || !(m1.umag < R(0.5))) atomicOr(status, 1);
-            collide<R, R, FR>(c, dr0.iphi, m0, d0, h0);
-            collide<R, R, FR>(c, dr1.iphi, m1, d1, h1);
+            collide<R, R, FR, IncForm<T>::value>(c, dr0.iphi, m0, d0, h0);
+            collide<R, R, FR, IncForm<T>::value>(c, dr1.iphi, m1, d1, h1);
             if constexpr (FR) {
                 typename FrameStore<T>::type k0, k1;
                 const R s0 = frame_make<T>(c, m0.dT, k0) - m0.F;  // exact: frame values
