@@ -91,7 +91,7 @@ def recorded_adjoint_instructions():
         return None
     vals = {}
     for line in text.splitlines():
-        if ":" in line and line.split(":", 1)[0] in ("kernel_sources_sha256", "warp_instructions_k_step2x",
+        if ":" in line and line.split(":", 1)[0] in ("kernel_sources_sha256", "warp_instructions_forward",
                                                       "warp_instructions_k_adjoint", "warp_instructions_k_adjoint_ring"):
             k, v = line.split(":", 1)
             vals[k] = v.strip()
@@ -459,7 +459,7 @@ def adjoint_leg(n=512, nsteps=2000, ckpt=100):
     ins = recorded_adjoint_instructions()
     if ins:
         nseg = -(-nsteps // ckpt)
-        total = ((2 * nsteps - nseg) * ins["warp_instructions_k_step2x"]
+        total = ((2 * nsteps - nseg) * ins["warp_instructions_forward"]
                  + nsteps * (ins["warp_instructions_k_adjoint"] + ins["warp_instructions_k_adjoint_ring"]))
         nsm = torch.cuda.get_device_properties(0).multi_processor_count
         try:
