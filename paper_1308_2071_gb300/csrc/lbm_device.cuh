@@ -277,6 +277,31 @@ template <class R> __host__ __device__ __forceinline__ R mom_y(const R (&d)[9]) 
     return (d[2] - d[4]) + ((d[5] + d[6]) - (d[7] + d[8]));
 }
 
+// FP16 flow storage: moves each FP32 flow value onto the half-precision grid
+// (13 low mantissa bits cleared) with the rounding threshold taken from the
+// low mantissa bits of two other populations of the node, instead of
+// rounding to nearest.  Those bits change from step to step and do not
+// depend on the value rounded, so the rounding error averages out over the
+// steps instead of repeating: rounded to nearest, a slowly changing value
+// is rounded the same way step after step, and the slow Darcy relaxation
+// integrates that bias into the velocity.  The store's conversion to half
+// is then exact (in half's normal range; below 2^-14 it rounds once more).
+// The threshold is added to the bit pattern, whose low 31 bits are the
+// magnitude for either sign.  NaN passes unchanged (infinities stay
+// infinite).
+__device__ __forceinline__ void dither_to_half(float (&v)[9]) {
+    uint32_t b[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) b[i] = __float_as_uint(v[i]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const uint32_t r = (b[(i + 1) % 9] ^ b[(i + 5) % 9]) & 0x1fffu;
+        const float m = __uint_as_float((b[i] + r) & 0xffffe000u);
+        v[i] = v[i] != v[i] ? v[i] : m;
+    }
+}
+template <class T> __host__ __device__ constexpr bool half_flow() { return std::is_same<typename T::SF, __half>::value; }
+
 // ---- per-launch coefficients ----------------------------------------------------
 
 // Everything a step needs besides the buffers, in the arithmetic type R.
@@ -983,6 +1008,7 @@ __device__ __forceinline__ void update_node(const Coef<typename T::R>& c, const 
     const Macro<R> mc = node_state<T, FIELD>(c, gm, src, phi, x, y, dr, d, h);
     if (!(mc.umag < R(0.5))) atomicOr(status, 1);  // also catches NaN
     collide<R, R, Framed<T>::value, IncForm<T>::value>(c, dr.iphi, mc, d, h);
+    if constexpr (half_flow<T>()) dither_to_half(d);
     const int off = y * gm.pitch + x;
     if constexpr (Framed<T>::value) frame_out<T>(c, gm, dst, off, mc, h);
     if (in_plane(gm, off)) {
@@ -1022,6 +1048,18 @@ __device__ __forceinline__ void collide_fluid_pair_x2(const Coef<float>& c, cons
     const Macro<F2> m = fluid_macros<F2, float, FR>(c, dr, d, h, F2(F0, F1));
     if (!(m.umag.v.x < 0.5f) || !(m.umag.v.y < 0.5f)) atomicOr(status, 1);
     collide<F2, float, FR>(c, dr.iphi, m, d, h);
+    if constexpr (half_flow<T>()) {
+        float v0[9], v1[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            v0[i] = d[i].v.x;
+            v1[i] = d[i].v.y;
+        }
+        dither_to_half(v0);
+        dither_to_half(v1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = F2(v0[i], v1[i]);
+    }
     if constexpr (FR) {
         typename FrameStore<T>::type k0, k1;
         const float s0 = frame_make<T>(c, m.dT.v.x, k0) - m.F.v.x;  // exact: frame values

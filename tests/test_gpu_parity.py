@@ -60,8 +60,12 @@ def field_errors(obs, o):
 
 # ---- one-step map, every population, several tiles and ragged tails ----------
 
+# f16: the flow values are moved onto the half-precision grid by a dithered
+# rounding, whose error stays below one unit of half precision (6.1e-5 for
+# |f_i - w_i rho0| < 0.125); the thermal values of its node pairs come from
+# paired FP32 instructions, which round every product (no fused multiply-add)
 @pytest.mark.parametrize("precision,tol_f,tol_g", [("f64", 1e-13, 1e-13), ("f32", 2e-7, 2e-7),
-                                                  ("f16", 3e-5, 2e-7), ("f32t", 2e-7, 2e-7)])
+                                                  ("f16", 6.2e-5, 3e-7), ("f32t", 2e-7, 2e-7)])
 @pytest.mark.parametrize("shape", [(17, 13), (64, 64), (131, 70), (300, 257)])
 @pytest.mark.parametrize("npt", [1, 2, 3])
 def test_one_step_populations(precision, tol_f, tol_g, shape, npt, nthreads):
@@ -271,7 +275,7 @@ def test_max_size_one_step_with_porosity_field(nthreads):
 
 # ---- full size, bench launch configuration ----------------------------------------
 
-@pytest.mark.parametrize("precision,tol_f,tol_g", [("f32", 2e-7, 2e-7), ("f16", 3e-5, 2e-7)])
+@pytest.mark.parametrize("precision,tol_f,tol_g", [("f32", 2e-7, 2e-7), ("f16", 6.2e-5, 2e-7)])
 def test_full_size_one_step(precision, tol_f, tol_g, nthreads):
     # 4096^2 cavity of the throughput benchmark (Ra = 1e6, Da = 1e-4, phi = 0.4)
     # in the launch shape the autotuner picks for it (the benchmark's): every
@@ -343,12 +347,13 @@ def test_planted_nan_raises_divergence_status():
 
 # ---- launch shapes and the autotuner -----------------------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-15), ("f32", 1e-7), ("f16", 3e-5)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-15), ("f32", 1e-7), ("f16", 6.2e-5)])
 @pytest.mark.parametrize("shape", [(17, 13), (131, 70)])
 def test_launch_shapes_agree_to_one_rounding(precision, tol, shape):
     # The two-nodes-per-thread kernel evaluates the same formulas; the compiler
     # may fuse multiply-adds differently, so one step from the same state
-    # agrees to within a rounding of the stored values.
+    # agrees to within a rounding of the stored values (f16: one unit of half
+    # precision, as the dithered rounding may go either way).
     nx, ny = shape
     ref = cavity(nx, ny, Ra=1e5, Da=1e-2, phi=0.6, precision=precision, nodes_per_thread=1)
     ref.step(200)
