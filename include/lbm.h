@@ -43,7 +43,13 @@ extern "C" {
  * plane: the node's T - T0 when it was last written), so that the stored
  * values stay small and FP32 keeps the slow late-time evolution of T (plain
  * FP32 deviations g_j - w~_j T0 of up to 0.3 lose changes below 3e-8 per
- * step).  Bytes moved per node and step: 224, 114, 78, 120. */
+ * step).  LBM_F32 and LBM_F32_FRAMED collide in increments (f + M^-1 (m+ -
+ * m), equal in exact arithmetic to Eq. 18), which keeps the rounded factors
+ * of M^-1 from biasing the momentum step after step.  LBM_F32_STORE_F16
+ * rounds the flow values to half precision with a threshold taken from other
+ * populations' low bits (dithered) instead of to nearest, so the rounding
+ * errors average out over the steps.  Bytes moved per node and step: 224,
+ * 114, 78, 120. */
 #define LBM_F64 0            /* FP64 storage, FP64 arithmetic                       */
 #define LBM_F32 1            /* FP32 storage, 8-bit temperature frame (a power-of-
                                 two quantum fq: F = k fq), FP32 arithmetic          */
