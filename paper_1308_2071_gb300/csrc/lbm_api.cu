@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -586,12 +587,20 @@ int lbm_tune(lbm_handle h, const char* cache_path, int* block_x, int* block_y, i
             h->npt = cd[2];
             int rc = advance(h, 3, false);
             if (rc != LBM_OK) return rc;
-            CK(h, cudaEventRecord(e0, h->stream));
-            if ((rc = advance(h, 30, false)) != LBM_OK) return rc;
-            CK(h, cudaEventRecord(e1, h->stream));
-            CK(h, cudaEventSynchronize(e1));
+            // 30 steps, or on small lattices as many as take about 2 ms (at most
+            // 2000), so that timer resolution and clock ramps do not pick the shape
+            long nsteps = 30;
             float ms = 0.f;
-            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(h, cudaEventRecord(e0, h->stream));
+                if ((rc = advance(h, nsteps, false)) != LBM_OK) return rc;
+                CK(h, cudaEventRecord(e1, h->stream));
+                CK(h, cudaEventSynchronize(e1));
+                CK(h, cudaEventElapsedTime(&ms, e0, e1));
+                if (pass == 1 || ms >= 2.f) break;
+                nsteps = std::min(2000L, (long)(nsteps * 2.f / std::max(ms, 1e-3f)) + 1);
+            }
+            ms *= 30.f / (float)nsteps;  // per 30 steps
             if (ms < best_ms) {
                 best_ms = ms;
                 best[0] = cd[0];
