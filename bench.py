@@ -44,9 +44,11 @@ METRIC = "coupled MLUPS & % HBM roofline, FP32 vs FP64 at stated Nu error; adjoi
 # FP16 variant 9 x 2 B (flow) + 5 x 4 B (thermal), each way
 # FP32 variants also read and write the node's temperature frame (1 byte, FP32 frame: 4)
 BYTES_PER_NODE = {"f64": 28 * 8, "f32": 28 * 4 + 2, "f16": 2 * (9 * 2 + 5 * 4 + 1), "f32t": 30 * 4}
-DTYPE = {"f64": "f64", "f32": "f32 storage with an 8-bit per-node temperature frame, f32 arithmetic",
-         "f16": "f16 flow + f32 thermal storage with an 8-bit temperature frame, f32 arithmetic",
-         "f32t": "f32 storage with an f32 per-node temperature frame, f32 arithmetic"}
+# arithmetic type of the path, and the storage it streams
+DTYPE = {"f64": "f64", "f32": "f32", "f16": "f32", "f32t": "f32"}
+STORAGE = {"f64": "f64 populations", "f32": "f32 populations, 8-bit per-node temperature frame",
+           "f16": "f16 flow (dithered rounding) and f32 thermal populations, 8-bit temperature frame",
+           "f32t": "f32 populations, f32 per-node temperature frame"}
 
 
 def parse():
@@ -603,7 +605,8 @@ def main():
                 algorithmic_bytes_per_launch=nodes * bpn, peak_source=peak_kind)
     line = dict(metric=METRIC, value=round(mlups, 2), unit="MLUPS", n_gpus=world, steps=a.steps,
                 warmup=a.warmup, ms_per_step=round(ms / a.steps, 5), higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype=DTYPE[a.precision], data="synthetic (seeded, no dataset)",
+                vs_baseline=None, dtype=DTYPE[a.precision], storage=STORAGE[a.precision],
+                data="synthetic (seeded, no dataset)",
                 config=dict(workload(a.size, a.field), parallelism="replicas" if world > 1 else "single GPU",
                             replicas=world),
                 roofline=roof, clocks=clocks, gpu_launches=a.steps, launch_shape=shapes.get(a.precision),
