@@ -158,6 +158,9 @@ __device__ __forceinline__ void tile_update(const Coef<typename T::R>& c, const 
 // descriptor in shared memory and every other coefficient from the kernel
 // parameter cu, which instructions read from the constant bank; without
 // SPLIT all come from the descriptor (about 45 values per tile in registers).
+// FP32 arithmetic: at most 80 registers (3 blocks of 256 threads, 6 of 128
+// per SM); the increment-form collision keeps the pulled values live and its
+// node-pair bodies spilled 250-290 bytes under 64.
 template <class T, int NPT, bool SPLIT>
 __global__ void __launch_bounds__(256, sizeof(typename T::R) == 4 ? 3 : 2)
     k_batch(const CavDesc<typename T::R>* __restrict__ cavs, const Tile* __restrict__ tiles, int ntiles, int lg_tw,
