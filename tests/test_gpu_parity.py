@@ -275,7 +275,9 @@ def test_max_size_one_step_with_porosity_field(nthreads):
 
 # ---- full size, bench launch configuration ----------------------------------------
 
-@pytest.mark.parametrize("precision,tol_f,tol_g", [("f32", 2e-7, 2e-7), ("f16", 6.2e-5, 2e-7)])
+# f16: one unit of half precision for the dithered flow values, and the paired
+# FP32 instructions of its node pairs (no fused multiply-add) for the thermal ones
+@pytest.mark.parametrize("precision,tol_f,tol_g", [("f32", 2e-7, 2e-7), ("f16", 6.2e-5, 3e-7)])
 def test_full_size_one_step(precision, tol_f, tol_g, nthreads):
     # 4096^2 cavity of the throughput benchmark (Ra = 1e6, Da = 1e-4, phi = 0.4)
     # in the launch shape the autotuner picks for it (the benchmark's): every
